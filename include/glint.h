@@ -1,0 +1,172 @@
+/*
+ * glint.h - C ABI of the GB300 (sm_103a) glint BRDF library.
+ *
+ * The library evaluates, per pixel of a G-buffer, the glint BRDF of
+ * Deliot & Belcour, "Real-Time Rendering of Glinty Appearances using
+ * Distributed Binomial Laws on Anisotropic Grids" (HPG 2023):
+ *   Sec. 3, Eq. 1-4  microfacet shading with the NDF replaced by a counting
+ *                    process D_P = D(n)/R * b(N(P), p) / N(P), p = R D(h)/D(n);
+ *   Sec. 4.2, Eq. 10 distributed binomial blending across two LODs;
+ *   Sec. 5           anisotropic virtual grids (scale, ratio, orientation);
+ *   Sec. 6.1-6.2     tetrahedral blending and simplex surface grids
+ *                    (48 binomial evaluations per pixel and light);
+ *   Sec. 6.3         gated Gaussian approximation of the binomial law.
+ *
+ * Conventions (all entry points):
+ *   - Pointers marked "device" are CUDA device pointers owned by the caller;
+ *     the library never frees them.  "host" pointers are read during the
+ *     call only, unless stated otherwise.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream).  Output buffers are valid
+ *     once the stream has reached the end of the enqueued work.
+ *   - Return value: GLINT_OK (0) or a negative GLINT_ERR_* code; no
+ *     exception crosses the interface.  Arguments are validated on the host
+ *     before anything is enqueued; on error nothing is enqueued.
+ *   - Pixels are row-major, x fastest.  Background pixels (normal = 0) and
+ *     invalid pixels produce 0.
+ */
+#ifndef GLINT_H
+#define GLINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GLINT_OK                   0
+#define GLINT_ERR_ARG             -1  /* null pointer, bad size or parameter */
+#define GLINT_ERR_ALIGN           -2  /* device pointer not 16-byte aligned */
+#define GLINT_ERR_NOT_DEVICE_PTR  -3  /* pointer is not device-accessible memory */
+#define GLINT_ERR_CUDA            -4  /* a CUDA runtime call failed */
+#define GLINT_ERR_UNSUPPORTED     -5  /* no sm_103a device, or parameter outside supported range */
+#define GLINT_ERR_WORKSPACE       -6  /* workspace or staging buffer too small */
+
+#define GLINT_MAX_LIGHTS   8
+#define GLINT_MAX_SUB      64
+#define GLINT_MAX_RINGS    6
+#define GLINT_MAX_LODS     16
+
+/* Material (Sec. 3 and Sec. 5-6 parameters).
+ *   ndf         0 Beckmann, 1 GGX (Sec. 7: any NDF converges).
+ *   alpha_x/y   NDF roughness along tangent / bitangent (ignored when a
+ *               per-pixel material plane is given).
+ *   ln_density  natural log of the flake density, flakes per unit uv^2
+ *               (ignored with a per-pixel plane).  Level 0 holds one flake
+ *               per texel (Sec. 4.1, stratified distribution).
+ *   R           Eq. 4 ratio, 0 < R <= 1 (Sec. 7 uses 0.034).
+ *   F0          Schlick reflectance at normal incidence.
+ *   gamma       angular texel size in projected half-vector units, >= 1e-3
+ *               (Sec. 5.2, "subdivide it to account for the glints'
+ *               micro-roughness").
+ *   n_lods      L, 2..16 levels of detail; level l holds f^l flakes per texel.
+ *   n_rings     M, 1..6 anisotropy rings; ring m has ratio 2^m and 2^(m+1)
+ *               orientations (Fig. 5).
+ *   lod_factor  f, area ratio between consecutive LODs: 2 or 4 (Eq. 13 writes
+ *               powers of two; Sec. 1 says consecutive LODs quadruple).
+ *   max_sub     K_max, 1..64: most sub-footprints one pixel is cut into when
+ *               its ratio exceeds 2^M or its area exceeds the top level.
+ *   seed        32-bit seed of the per-texel hash. */
+typedef struct GlintMaterial {
+    int32_t  ndf;
+    float    alpha_x, alpha_y;
+    float    ln_density;
+    float    R;
+    float    F0;
+    float    gamma;
+    int32_t  n_lods;
+    int32_t  n_rings;
+    int32_t  lod_factor;
+    int32_t  max_sub;
+    uint32_t seed;
+} GlintMaterial;
+
+/* Punctual light (Sec. 8: point lights only; cost linear in lights).
+ *   kind 0: point light; direction (towards the light) and irradiance-scaled
+ *           intensity E are read per pixel from the frame's light plane.
+ *   kind 1: directional light; dir (towards the light, any length > 0) and
+ *           intensity apply to every pixel. */
+typedef struct GlintLight {
+    int32_t kind;
+    float   dir[3];
+    float   intensity;
+} GlintLight;
+
+/* One frame of G-buffer, all planes device pointers, 16-byte aligned.
+ *   gbuf      [height][width][16] float: u, v, du/dx, dv/dx, du/dy, dv/dy,
+ *             n.xyz, t.xyz, towards-viewer.xyz, 0.  n = 0 marks background.
+ *   light_px  [n_lights][height][width][4] float: per-pixel (direction to the
+ *             light xyz, E) for lights of kind 0; may be NULL when every light
+ *             is directional.
+ *   mat_px    [height][width][2] float: per-pixel (alpha, flakes per uv^2),
+ *             isotropic alpha; NULL to use the scalar material. */
+typedef struct GlintFrame {
+    const float* gbuf;
+    const float* light_px;
+    const float* mat_px;
+    int32_t width, height;
+    int32_t n_lights;
+} GlintFrame;
+
+/* Human-readable text of an error code (static string). */
+const char* glint_error_string(int code);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int glint_version(void);
+
+/* Plain forward evaluation of one frame (Sec. 3-6, whole hot path):
+ * out[y][x] = sum over lights of F G D_P E / (4 <n.w_v>).
+ *   out: device, [height][width] float, written completely.
+ * Errors: GLINT_ERR_ARG (null, sizes <= 0, width*height > 2^31-1,
+ * n_lights out of [0, 8], light_px NULL with a kind-0 light, material out of
+ * range), GLINT_ERR_ALIGN, GLINT_ERR_NOT_DEVICE_PTR, GLINT_ERR_CUDA. */
+int glint_eval(const GlintFrame* frame, const GlintMaterial* material,
+               const GlintLight* lights, float* out, void* stream);
+
+/* The same evaluation with host buffers: copies every plane of `frame`
+ * (host pointers, ideally pinned) into `staging` (device, caller-owned, at
+ * least glint_eval_host_staging_size() bytes), evaluates, and copies the
+ * image back to `out` (host).  The copies are enqueued on `stream`; the
+ * caller synchronises before reading `out`. */
+size_t glint_eval_host_staging_size(int32_t width, int32_t height, int32_t n_lights,
+                                    int32_t has_light_plane, int32_t has_material_plane);
+int glint_eval_host(const GlintFrame* host_frame, const GlintMaterial* material,
+                    const GlintLight* lights, float* out_host,
+                    void* staging, size_t staging_bytes, void* stream);
+
+/* Parity trace of selected pixels: for each listed pixel, a summary and the
+ * records of every binomial evaluation in the canonical order (light,
+ * sub-footprint, tetrahedron vertex 0..3, simplex vertex 0..2, angular
+ * texel 0..3), i.e. record index ((light*K + sub)*4 + vert)*12 + sv*4 + av.
+ *   px:   device, n_px int32 flat pixel indices.
+ *   pix:  device, n_px records.
+ *   recs: device, n_px * rec_cap records; pixel k owns recs[k*rec_cap ...];
+ *         records beyond rec_cap are not written (pix.n_rec holds the total). */
+typedef struct GlintTracePix {
+    int32_t status;          /* 0 shaded, 1 background, 2 invalid, 3 lattice out of range */
+    int32_t K;               /* sub-footprints */
+    int32_t n_rec;           /* records produced (may exceed rec_cap) */
+    int32_t pad;
+    float   A, r, phi, out;  /* flakes in footprint, ratio, orientation, radiance */
+} GlintTracePix;
+
+typedef struct GlintTraceRec {
+    int32_t  light, sub, vert, sv, av;
+    uint32_t grid_id;        /* (level << 16) | (ring << 8) | orientation */
+    int32_t  i, j;           /* simplex lattice vertex */
+    int32_t  ax, ay;         /* angular texel */
+    uint32_t h0, h1;         /* hash words (gate, Gaussian) */
+    int32_t  gate, c;        /* gate decision, integer count */
+    float    n, P1, mu, sigma, c_cont, u, v, p;
+} GlintTraceRec;
+
+int glint_eval_trace(const GlintFrame* frame, const GlintMaterial* material,
+                     const GlintLight* lights, const int32_t* px, int32_t n_px,
+                     GlintTracePix* pix, GlintTraceRec* recs, int32_t rec_cap, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLINT_H */

@@ -262,7 +262,10 @@ Footprint footprint(double a, double b, double c, double d) {
     if (phi < 0.0) phi += M_PI;
     if (phi >= M_PI) phi -= M_PI;
     fp.phi = phi;
-    fp.r = fp.P > 0.0 ? s0sq / fp.P : INFINITY;
+    /* ratio sigma0 / max(sigma1, 2^-20 sigma0): a line-like footprint keeps a
+     * finite ratio (beyond 2^20 nothing changes: the sub-footprint count is
+     * capped and the ring coordinate clamped at M). */
+    fp.r = (fp.P > 0.0 && s0sq < 0x1p20 * fp.P) ? s0sq / fp.P : 0x1p20;
     return fp;
 }
 
@@ -487,9 +490,9 @@ T gated_count(const CountLaw<T>& L, double th0, double th1, bool relaxed,
     *z = phi_inv(th1);
     const T cc = 1.0 + L.mu + L.sigma * (*z);
     *c_cont = val(cc);
-    const double fl = std::floor(val(cc));
-    *c_int = (int)std::min(std::max(fl, 1.0), L.nceil);
-    if (!relaxed) return T((double)*c_int);
+    const double c = std::min(std::max(std::floor(val(cc)), 1.0), L.nceil);
+    *c_int = c < 2147483647.0 ? (int)c : 2147483647;      /* trace value only */
+    if (!relaxed) return T(c);
     if (val(cc) <= 1.0) return T(1.0);
     if (val(cc) >= L.nceil) return T(L.nceil);
     return cc;
@@ -716,7 +719,7 @@ int check_material(const OMaterial* m, int nL) {
     if (m->n_rings < 1 || m->n_rings > 6) return -1;
     if (m->lod_factor != 2 && m->lod_factor != 4) return -1;
     if (m->max_sub < 1 || m->max_sub > 64) return -1;
-    if (!(m->R > 0.0f && m->R <= 1.0f) || !(m->gamma > 0.0f)) return -1;
+    if (!(m->R > 0.0f && m->R <= 1.0f) || !(m->gamma >= 1e-3f)) return -1;
     if (nL < 0 || nL > 8) return -1;
     return 0;
 }

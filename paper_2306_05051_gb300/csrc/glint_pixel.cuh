@@ -1,0 +1,471 @@
+// Per-pixel glint BRDF evaluation (device code), Deliot & Belcour 2023.
+//
+// One pixel, in the paper's order:
+//   1. shading frame from the G-buffer                         (Sec. 3)
+//   2. footprint: SVD of dUV/d(x,y) -> area, ratio, orientation (Sec. 5.1)
+//   3. sub-footprints when the ratio or area leaves the grids   (Sec. 4.2 ext.)
+//   4. LOD bracket with area-linear coordinate                   (Sec. 5.2, Eq. 13)
+//   5. ratio/orientation cell, pentagon triangle, prism tetrahedron
+//      -> 4 grids with trials w_i f^l_i                          (Fig. 5, Sec. 6.1)
+//   6. per grid: anisotropic transform + simplex lattice -> 3 texels (Eq. 12, Sec. 6.2)
+//   7. per light: NDF ratio p, angular texels (4), hash, gated
+//      binomial counts (48 per light), interpolation of realisations
+//                                                                (Eq. 4, Eq. 14, Sec. 6.3)
+//   8. D_P = D(n)/R * C / A and the microfacet BRDF             (Eq. 2-3)
+// Steps 2-6 run in double-float (see glint_df.cuh), the per-light and
+// per-evaluation work in FP32 and 32-bit integers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "glint_df.cuh"
+
+namespace glint {
+
+constexpr int kMaxLights = 8;
+constexpr int kMaxRings = 6;
+constexpr int kRotEntries = (1 << (kMaxRings + 2)) - 3;   // rings 0..6
+
+__host__ __device__ constexpr int rot_entries(int M) { return (1 << (M + 2)) - 3; }
+__host__ __device__ constexpr int rot_index(int ring, int kor) { return ring == 0 ? 0 : (1 << (ring + 1)) - 3 + kor; }
+
+// Per (ring, orientation): the 2x2 map uv -> simplex lattice coordinate,
+// up to the per-level factor sqrt(rho) f^(-l/2):
+//   Q = 3^(-1/4) S diag(2^(-m/2), 2^(m/2)) Rot(-phi_k),  S = I + F2 [[1,1],[1,1]],
+// stored as double-float entries (q00, q01 | q10, q11).
+struct RotEntry {
+    float4 r0;   // q00.hi, q00.lo, q01.hi, q01.lo
+    float4 r1;   // q10.hi, q10.lo, q11.hi, q11.lo
+};
+
+struct Tables {
+    DfTables d;
+    RotEntry rot[kRotEntries];
+};
+
+struct KLight {
+    int32_t kind;
+    float dx, dy, dz, E;
+};
+
+struct KParams {
+    const float4* gbuf;
+    const float4* light_px;
+    const float2* mat_px;
+    float* out;
+    int32_t W, H, npx, nL;
+    KLight lights[kMaxLights];
+    int32_t ndf;
+    float ax, ay;
+    float2 rho, sqrt_rho;        // double-float of exp(ln_density) and its root
+    float R, F0, gamma;
+    int32_t L, M, f, Kmax;
+    uint32_t seed;
+    float top;                   // f^(L-1)
+    int32_t log2f;               // log2(f): 1 or 2
+    Tables tables;
+};
+
+// --------------------------------------------------------------------------
+// hash: pcg3d / pcg4d (Jarzynski & Olano, JCGT 2020), MurmurHash3 fmix32
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void pcg4d(uint32_t& x, uint32_t& y, uint32_t& z, uint32_t& w) {
+    x = x * 1664525u + 1013904223u; y = y * 1664525u + 1013904223u;
+    z = z * 1664525u + 1013904223u; w = w * 1664525u + 1013904223u;
+    x += y * w; y += z * x; z += x * y; w += y * z;
+    x ^= x >> 16; y ^= y >> 16; z ^= z >> 16; w ^= w >> 16;
+    x += y * w; y += z * x; z += x * y; w += y * z;
+}
+
+__device__ __forceinline__ void pcg3d(uint32_t& x, uint32_t& y, uint32_t& z) {
+    x = x * 1664525u + 1013904223u; y = y * 1664525u + 1013904223u; z = z * 1664525u + 1013904223u;
+    x += y * z; y += z * x; z += x * y;
+    x ^= x >> 16; y ^= y >> 16; z ^= z >> 16;
+    x += y * z; y += z * x; z += x * y;
+}
+
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16; h *= 0x85EBCA6Bu;
+    h ^= h >> 13; h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Standard normal quantile of theta = ((h >> 8) + 1/2) 2^-24, computed on
+// the lower half so every theta is exact in FP32: Phi^-1(1 - x) = -Phi^-1(x).
+__device__ __forceinline__ float normal_of_word(uint32_t h) {
+    const uint32_t k = h >> 8;
+    const bool upper = k >= (1u << 23);
+    const uint32_t m = upper ? ((1u << 24) - 1u - k) : k;
+    const float x = __fmul_rn(__fadd_rn((float)m, 0.5f), 5.9604644775390625e-8f);   // 2^-24
+    const float z = normcdfinvf(x);
+    return upper ? -z : z;
+}
+
+// --------------------------------------------------------------------------
+// material functions
+// --------------------------------------------------------------------------
+__device__ __forceinline__ float smith_lambda(int ndf, float ax, float ay, float wt, float wb, float wn) {
+    const float s2 = (wt * ax) * (wt * ax) + (wb * ay) * (wb * ay);
+    if (!(s2 > 0.0f)) return 0.0f;
+    const float a = wn * rsqrtf(s2);
+    if (ndf == 0) return -0.5f * erfcf(a) + expf(-a * a) / (3.5449077018110318f * a);   // 2 sqrt(pi)
+    return 0.5f * (sqrtf(1.0f + 1.0f / (a * a)) - 1.0f);
+}
+
+struct Vert {           // one tetrahedron vertex (a virtual grid)
+    int ring, kor, level;
+};
+
+// --------------------------------------------------------------------------
+// sinks: the image kernel ignores everything, the trace kernel records
+// --------------------------------------------------------------------------
+struct NoSink {
+    static constexpr bool kTrace = false;
+    __device__ void pix(int, int, float, float, float, float) {}
+    __device__ void rec(int, int, int, int, int, int, uint32_t, int, int, int, int, uint32_t, uint32_t,
+                        int, int, float, float, float, float, float, float, float, float) {}
+};
+
+struct LightState {
+    bool on;
+    float p, shade;
+    float v[4];
+    uint32_t A0[4], A1[4];
+    int32_t ax[4], ay[4];
+};
+
+template <int NLT, class Sink>
+__device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& sink) {
+    const int nL = NLT > 0 ? NLT : P.nL;
+    const float4* g = P.gbuf + (size_t)px * 4;
+    const float4 g0 = __ldg(g), g1 = __ldg(g + 1), g2 = __ldg(g + 2), g3 = __ldg(g + 3);
+    const float gv[15] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z};
+    bool finite = true;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) finite &= isfinite(gv[k]);
+    if (!finite) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+
+    // ---- 1. shading frame ------------------------------------------------
+    float n[3] = {g1.z, g1.w, g2.x};
+    if (n[0] == 0.0f && n[1] == 0.0f && n[2] == 0.0f) { sink.pix(1, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+    float tg[3] = {g2.y, g2.z, g2.w};
+    float wv[3] = {g3.x, g3.y, g3.z};
+    {
+        const float inl = 1.0f / sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        n[0] *= inl; n[1] *= inl; n[2] *= inl;
+    }
+    const float tn = tg[0] * n[0] + tg[1] * n[1] + tg[2] * n[2];
+    tg[0] -= tn * n[0]; tg[1] -= tn * n[1]; tg[2] -= tn * n[2];
+    const float tl = sqrtf(tg[0] * tg[0] + tg[1] * tg[1] + tg[2] * tg[2]);
+    const float vl = sqrtf(wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2]);
+    if (!(tl > 0.0f) || !(vl > 0.0f)) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+    tg[0] /= tl; tg[1] /= tl; tg[2] /= tl;
+    wv[0] /= vl; wv[1] /= vl; wv[2] /= vl;
+    const float b[3] = {n[1] * tg[2] - n[2] * tg[1], n[2] * tg[0] - n[0] * tg[2], n[0] * tg[1] - n[1] * tg[0]};
+    const float cos_v = wv[0] * n[0] + wv[1] * n[1] + wv[2] * n[2];
+    if (!(cos_v > 0.0f)) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+
+    float ax = P.ax, ay = P.ay;
+    df rho = ldf(P.rho), srho = ldf(P.sqrt_rho);
+    if (P.mat_px) {
+        const float2 mp = __ldg(P.mat_px + px);
+        ax = ay = mp.x;
+        rho = mkdf(mp.y);
+        srho = dfsqrt(rho);
+    }
+
+    // ---- 2. footprint (double-float) ----------------------------------
+    // J = [[a, b], [c, d]] = [[du/dx, du/dy], [dv/dx, dv/dy]], pre-scaled by
+    // a power of two so its squares stay well inside FP32 range.
+    float ja = g0.z, jb = g1.x, jc = g0.w, jd = g1.y;
+    int je;
+    frexpf(fmaxf(fmaxf(fabsf(ja), fabsf(jb)), fmaxf(fabsf(jc), fabsf(jd))), &je);
+    {
+        const float s = pow2f(-je);
+        ja *= s; jb *= s; jc *= s; jd *= s;
+    }
+    const df E = two_prod(ja, ja) + two_prod(jb, jb);
+    const df G = two_prod(jc, jc) + two_prod(jd, jd);
+    const df F = two_prod(ja, jc) + two_prod(jb, jd);
+    const df det = dfabs(two_prod(ja, jd) - two_prod(jc, jb));
+    const df Pft = scale2(det, 2 * je);                 // |det J| in uv^2
+    const df A = Pft * rho;                             // flakes in the footprint
+    if (!(A.hi > 0.0f)) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+    const df hm = scale2(E - G, -1);
+    const df hyp = dfsqrt(hm * hm + F * F);
+    const df s0sq = scale2(E + G, -1) + hyp;
+    // ratio sigma0 / max(sigma1, 2^-20 sigma0): finite for line-like footprints
+    const df ratio = dflt(s0sq, scale2(det, 20)) ? s0sq / det : mkdf(1048576.0f);
+    df phi = scale2(dfatan2(scale2(F, 1), E - G, T.d), -1);
+    if (dfsign(phi) < 0) phi = phi + ldf(T.d.pi);
+    if (!dflt(phi, ldf(T.d.pi))) phi = phi - ldf(T.d.pi);
+    const float s0f = sqrtf(s0sq.hi) * pow2f(je);
+    const float s1f = Pft.hi / s0f;
+
+    // ---- 3. sub-footprints --------------------------------------------
+    int Kmaj = 1;
+    const df rq = scale2(ratio, -P.M);
+    if (dfsign(rq - 1.0f) > 0) {
+        df fr;
+        float c = dffloor(rq, &fr);
+        if (dfsign(fr) > 0) c += 1.0f;
+        Kmaj = c >= (float)P.Kmax ? P.Kmax : (int)c;
+    }
+    const df Ap = A / (float)Kmaj;
+    int ksub = 1;
+    while (dflt(mkdf((float)(ksub * ksub) * P.top), Ap) && Kmaj * (ksub + 1) * (ksub + 1) <= P.Kmax) ++ksub;
+    const int K = Kmaj * ksub * ksub;
+    const df As = A / (float)K;
+    const df rho_r = dflog2(ratio, T.d) - dflog2(mkdf((float)Kmaj), T.d);
+    sink.pix(0, K, A.hi, ratio.hi, phi.hi, 0.0f);
+
+    // ---- 4. LOD bracket -------------------------------------------------
+    int level;
+    df s;
+    bool pinned;
+    if (dflt(As, 1.0f)) { level = 0; s = mkdf(0.0f); pinned = true; }
+    else if (!dflt(As, P.top)) { level = P.L - 2; s = mkdf(1.0f); pinned = true; }
+    else {
+        level = 0;
+        float fl = 1.0f;
+        while (!dflt(As, fl * (float)P.f)) { fl *= (float)P.f; ++level; }
+        const df x = scale2(As, -level * P.log2f) - 1.0f;
+        s = P.f == 4 ? x * ldf(T.d.third) : x;
+        pinned = false;
+    }
+
+    // ---- 5. ratio / orientation cell, triangle, tetrahedron --------------
+    df rr = rho_r;
+    if (dfsign(rr) < 0) rr = mkdf(0.0f);
+    if (!dflt(rr, (float)P.M)) rr = mkdf((float)P.M);
+    df fx_unused;
+    int m = (int)dffloor(rr, &fx_unused);
+    if (m > P.M - 1) m = P.M - 1;
+    const df x = rr - (float)m;
+    const int nm = m == 0 ? 4 : (1 << (m + 1));
+    df t;
+    int a = (int)dffloor(scale2(phi * ldf(T.d.inv_pi), m == 0 ? 2 : m + 1), &t);
+    a %= nm;
+    Vert tv[3];
+    df lam[3];
+    if (m == 0) {
+        tv[0] = {0, 0, 0}; tv[1] = {1, a, 0}; tv[2] = {1, (a + 1) & 3, 0};
+        lam[0] = 1.0f - x;
+        lam[1] = x * (1.0f - t);
+        lam[2] = x * t;
+    } else {
+        const Vert P00 = {m, a, 0}, P01 = {m, (a + 1) % nm, 0};
+        const Vert P10 = {m + 1, 2 * a, 0}, P1h = {m + 1, 2 * a + 1, 0}, P11 = {m + 1, (2 * a + 2) % (2 * nm), 0};
+        const df xh = scale2(x, -1);
+        if (dfle(t, xh)) {
+            tv[0] = P00; tv[1] = P10; tv[2] = P1h;
+            lam[0] = 1.0f - x; lam[1] = x - scale2(t, 1); lam[2] = scale2(t, 1);
+        } else if (dfle(t, 1.0f - xh)) {
+            tv[0] = P00; tv[1] = P1h; tv[2] = P01;
+            lam[0] = (1.0f - t) - xh; lam[1] = x; lam[2] = t - xh;
+        } else {
+            const df omt = 1.0f - t;
+            tv[0] = P1h; tv[1] = P01; tv[2] = P11;
+            lam[0] = scale2(omt, 1); lam[1] = 1.0f - x; lam[2] = x - scale2(omt, 1);
+        }
+    }
+    // prism split by vertex order: upper weight of vertex j = clamp(s - C_j, 0, lam_j)
+    int vtri[4], vup[4], tet;
+    df w[4];
+    const df C1 = lam[0], C2 = lam[0] + lam[1];
+    if (dfle(s, C1)) {
+        tet = 1;
+        vtri[0] = 0; vup[0] = 0; w[0] = lam[0] - s;
+        vtri[1] = 1; vup[1] = 0; w[1] = lam[1];
+        vtri[2] = 2; vup[2] = 0; w[2] = lam[2];
+        vtri[3] = 0; vup[3] = 1; w[3] = s;
+    } else if (dfle(s, C2)) {
+        tet = 2;
+        vtri[0] = 1; vup[0] = 0; w[0] = lam[1] - (s - C1);
+        vtri[1] = 2; vup[1] = 0; w[1] = lam[2];
+        vtri[2] = 0; vup[2] = 1; w[2] = lam[0];
+        vtri[3] = 1; vup[3] = 1; w[3] = s - C1;
+    } else {
+        tet = 3;
+        vtri[0] = 2; vup[0] = 0; w[0] = lam[2] - (s - C2);
+        vtri[1] = 0; vup[1] = 1; w[1] = lam[0];
+        vtri[2] = 1; vup[2] = 1; w[2] = lam[1];
+        vtri[3] = 2; vup[3] = 1; w[3] = s - C2;
+    }
+    Vert vert[4];
+    float ntr[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        vert[i] = tv[vtri[i]];
+        vert[i].level = level + vup[i];
+        const df ni = pinned ? w[i] * As : scale2(w[i], vert[i].level * P.log2f);
+        ntr[i] = ni.hi;
+    }
+    (void)tet;
+
+    // ---- 7a. per-light state (independent of the sub-footprint) ---------
+    constexpr int NLA = NLT > 0 ? NLT : kMaxLights;
+    LightState ls[NLA];
+    const float Dn = 1.0f / (3.14159265358979f * ax * ay);
+    const float lam_v = smith_lambda(P.ndf, ax, ay, wv[0] * tg[0] + wv[1] * tg[1] + wv[2] * tg[2],
+                                     wv[0] * b[0] + wv[1] * b[1] + wv[2] * b[2], cos_v);
+#pragma unroll
+    for (int l = 0; l < NLA; ++l) {
+        LightState& L = ls[l];
+        L.on = false;
+        if (l >= nL) continue;
+        const KLight kl = P.lights[l];
+        float wl[3], E;
+        if (kl.kind == 0) {
+            const float4 lp = __ldg(P.light_px + (size_t)l * P.npx + px);
+            wl[0] = lp.x; wl[1] = lp.y; wl[2] = lp.z; E = lp.w;
+        } else {
+            wl[0] = kl.dx; wl[1] = kl.dy; wl[2] = kl.dz; E = kl.E;
+        }
+        const float wll = sqrtf(wl[0] * wl[0] + wl[1] * wl[1] + wl[2] * wl[2]);
+        if (!(wll > 0.0f)) continue;
+        wl[0] /= wll; wl[1] /= wll; wl[2] /= wll;
+        const float cos_l = wl[0] * n[0] + wl[1] * n[1] + wl[2] * n[2];
+        if (!(cos_l > 0.0f)) continue;
+        float h[3] = {wv[0] + wl[0], wv[1] + wl[1], wv[2] + wl[2]};
+        const float hl = sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+        h[0] /= hl; h[1] /= hl; h[2] /= hl;
+        const float ht = h[0] * tg[0] + h[1] * tg[1] + h[2] * tg[2];
+        const float hb = h[0] * b[0] + h[1] * b[1] + h[2] * b[2];
+        const float hn = h[0] * n[0] + h[1] * n[1] + h[2] * n[2];
+        // Eq. 4: p = R D(h) / D(n)
+        const float e = (ht / ax) * (ht / ax) + (hb / ay) * (hb / ay);
+        const float hn2 = hn * hn;
+        const float rat = P.ndf == 0 ? expf(-e / hn2) / (hn2 * hn2) : 1.0f / ((e + hn2) * (e + hn2));
+        L.p = fminf(P.R * rat, 1.0f);
+        // Eq. 14: bilinear angular texels of the projected half-vector
+        const float afx = ht / P.gamma, afy = hb / P.gamma;
+        const float fax = floorf(afx), fay = floorf(afy);
+        const float fx = afx - fax, fy = afy - fay;
+        const int ix = (int)fax, iy = (int)fay;
+        L.v[0] = (1.0f - fx) * (1.0f - fy); L.v[1] = fx * (1.0f - fy);
+        L.v[2] = (1.0f - fx) * fy;          L.v[3] = fx * fy;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            L.ax[k] = ix + (k & 1); L.ay[k] = iy + (k >> 1);
+            uint32_t hx = (uint32_t)L.ax[k], hy = (uint32_t)L.ay[k], hz = ~P.seed;
+            pcg3d(hx, hy, hz);
+            L.A0[k] = hx; L.A1[k] = hy;
+        }
+        // Eq. 2 with D_P = D(n)/R C/A: out_l = F G D(n) E / (4 R cos_v) * C / A
+        const float vh = wv[0] * h[0] + wv[1] * h[1] + wv[2] * h[2];
+        const float om = 1.0f - vh;
+        const float Fr = P.F0 + (1.0f - P.F0) * (om * om) * (om * om) * om;
+        const float lam_l = smith_lambda(P.ndf, ax, ay, wl[0] * tg[0] + wl[1] * tg[1] + wl[2] * tg[2],
+                                         wl[0] * b[0] + wl[1] * b[1] + wl[2] * b[2], cos_l);
+        const float Gs = 1.0f / ((1.0f + lam_v) * (1.0f + lam_l));
+        L.shade = Fr * Gs * Dn * E / (4.0f * P.R * cos_v);
+        L.on = true;
+    }
+
+    // ---- 6/7b. sub-footprints x lights x 48 evaluations ----------------
+    float C[NLA];
+#pragma unroll
+    for (int l = 0; l < NLA; ++l) C[l] = 0.0f;
+    const int ncols = Kmaj * ksub;
+    float sph, cph;
+    sincosf(phi.hi, &sph, &cph);
+    const float u0 = g0.x, v0 = g0.y;
+    int status = 0;
+    for (int sub = 0; sub < K && status == 0; ++sub) {
+        const int ia = sub % ncols, ib = sub / ncols;
+        const float oa = ((float)ia + 0.5f) / (float)ncols - 0.5f;
+        const float ob = ((float)ib + 0.5f) / (float)ksub - 0.5f;
+        const df us = two_sum(u0, s0f * oa * cph - s1f * ob * sph);
+        const df vs = two_sum(v0, s0f * oa * sph + s1f * ob * cph);
+        uint32_t S0[4][3], S1[4][3];
+        float uw[4][3];
+        int32_t li[4][3], lj[4][3];
+        uint32_t gid[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const Vert V = vert[i];
+            gid[i] = ((uint32_t)V.level << 16) | ((uint32_t)V.ring << 8) | (uint32_t)V.kor;
+            const RotEntry Q = T.rot[rot_index(V.ring, V.kor)];
+            df sl;
+            if (P.f == 4) sl = scale2(srho, -V.level);
+            else sl = (V.level & 1) ? scale2(srho * ldf(T.d.inv_sqrt2), -(V.level >> 1)) : scale2(srho, -(V.level >> 1));
+            const df qx = sl * (df{Q.r0.x, Q.r0.y} * us + df{Q.r0.z, Q.r0.w} * vs);
+            const df qy = sl * (df{Q.r1.x, Q.r1.y} * us + df{Q.r1.z, Q.r1.w} * vs);
+            if (!(fabsf(qx.hi) < 1073741824.0f) || !(fabsf(qy.hi) < 1073741824.0f)) { status = 3; break; }
+            df fxd, fyd;
+            const int i0 = (int)dffloor(qx, &fxd);
+            const int j0 = (int)dffloor(qy, &fyd);
+            const float fx = fxd.hi, fy = fyd.hi;
+            if (!dflt(fxd, fyd)) {
+                li[i][0] = i0;     lj[i][0] = j0;     uw[i][0] = 1.0f - fx;
+                li[i][1] = i0 + 1; lj[i][1] = j0;     uw[i][1] = fx - fy;
+                li[i][2] = i0 + 1; lj[i][2] = j0 + 1; uw[i][2] = fy;
+            } else {
+                li[i][0] = i0;     lj[i][0] = j0;     uw[i][0] = 1.0f - fy;
+                li[i][1] = i0;     lj[i][1] = j0 + 1; uw[i][1] = fy - fx;
+                li[i][2] = i0 + 1; lj[i][2] = j0 + 1; uw[i][2] = fx;
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                uint32_t hx = (uint32_t)li[i][j], hy = (uint32_t)lj[i][j], hz = gid[i], hw = P.seed;
+                pcg4d(hx, hy, hz, hw);
+                S0[i][j] = hx; S1[i][j] = hy;
+            }
+        }
+        if (status) break;
+#pragma unroll
+        for (int l = 0; l < NLA; ++l) {
+            if (!ls[l].on) continue;
+            const LightState& L = ls[l];
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                // Sec. 6.3: gated Gaussian binomial with N = n_i trials
+                const float nn = ntr[i];
+                float P1 = 0.0f;
+                if (nn > 0.0f && L.p > 0.0f) P1 = L.p >= 1.0f ? 1.0f : -expm1f(nn * log1pf(-L.p));
+                const uint32_t Tg = (uint32_t)ceilf(P1 * 33554432.0f);      // 2^25
+                const float nm1 = nn > 1.0f ? nn - 1.0f : 0.0f;
+                const float mu = nm1 * L.p;
+                const float var = mu * (1.0f - L.p);
+                const float sig = var > 0.0f ? sqrtf(var) : 0.0f;
+                const float nceil = ceilf(nn);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t h0 = fmix32(S0[i][j] + L.A0[k]);
+                        // theta0 < P1  <=>  2 (h0 >> 8) + 1 < P1 2^25
+                        const bool gate = ((h0 >> 7) | 1u) < Tg;
+                        float c = 0.0f;
+                        float cc = 0.0f;
+                        uint32_t h1 = 0;
+                        if (gate || Sink::kTrace) h1 = fmix32(S1[i][j] + L.A1[k]);
+                        if (gate) {
+                            cc = 1.0f + mu + sig * normal_of_word(h1);
+                            c = fminf(fmaxf(floorf(cc), 1.0f), nceil);
+                            acc += uw[i][j] * L.v[k] * c;
+                        }
+                        if (Sink::kTrace)
+                            sink.rec((((l * K + sub) * 4 + i) * 3 + j) * 4 + k, l, sub, i, j, k, gid[i],
+                                     li[i][j], lj[i][j], L.ax[k], L.ay[k], h0, h1, gate ? 1 : 0,
+                                     c < 2147483647.0f ? (int)c : 2147483647,
+                                     nn, P1, mu, sig, cc, uw[i][j], L.v[k], L.p);
+                    }
+                }
+            }
+            C[l] += acc;
+        }
+    }
+    if (status) { sink.pix(status, K, A.hi, ratio.hi, phi.hi, 0.0f); return 0.0f; }
+    float out = 0.0f;
+#pragma unroll
+    for (int l = 0; l < NLA; ++l)
+        if (ls[l].on) out += ls[l].shade * C[l];
+    out = out / A.hi;
+    sink.pix(0, K, A.hi, ratio.hi, phi.hi, out);
+    return out;
+}
+
+}  // namespace glint

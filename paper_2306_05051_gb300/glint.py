@@ -1,0 +1,116 @@
+"""Python API over the C ABI (include/glint.h).  PyTorch provides device
+memory and streams; every step of the glint evaluation runs in libglint.so.
+
+    img = render(gbuf, light_px, mat_px, material, lights)      # device tensors
+    img = render_scene(scene)
+    pix, recs = trace(scene, pixels)                             # parity records
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from .scenes import Light, Material, Scene
+
+
+def _stream_handle(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _check_plane(t, name, shape_tail, device=None, host=False):
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 tensor")
+    if host:
+        if t.is_cuda:
+            raise ValueError(f"{name} must be a host tensor")
+    elif not t.is_cuda or (device is not None and t.device != device):
+        raise ValueError(f"{name} must live on {device}")
+    if tuple(t.shape[-len(shape_tail):]) != tuple(shape_tail):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected [..., {shape_tail}]")
+
+
+def render(gbuf: torch.Tensor, light_px: Optional[torch.Tensor] = None, mat_px: Optional[torch.Tensor] = None,
+           material: Material = Material(), lights: Sequence[Light] = (), out: Optional[torch.Tensor] = None,
+           stream=None) -> torch.Tensor:
+    """Glint radiance [H, W] of one G-buffer frame (glint_eval)."""
+    _check_plane(gbuf, "gbuf", (16,))
+    dev = gbuf.device
+    H, W = int(gbuf.shape[0]), int(gbuf.shape[1])
+    _check_plane(light_px, "light_px", (H, W, 4), dev)
+    _check_plane(mat_px, "mat_px", (H, W, 2), dev)
+    if out is None:
+        out = torch.empty(H, W, dtype=torch.float32, device=dev)
+    _check_plane(out, "out", (H, W), dev)
+    frame = _lib.frame_struct(gbuf, light_px, mat_px, len(lights))
+    mat = _lib.material_struct(material)
+    lts = _lib.lights_struct(lights)
+    with torch.cuda.device(dev):
+        rc = _lib.lib().glint_eval(C.byref(frame), C.byref(mat), lts, out.data_ptr(), _stream_handle(stream))
+    _lib.check(rc, "glint_eval")
+    return out
+
+
+def render_scene(scene: Scene, out=None, stream=None, material=None, lights=None) -> torch.Tensor:
+    return render(scene.gbuf, scene.light_px, scene.mat_px, material or scene.material,
+                  scene.lights if lights is None else lights, out=out, stream=stream)
+
+
+def staging_bytes(scene: Scene) -> int:
+    return int(_lib.lib().glint_eval_host_staging_size(scene.width, scene.height, len(scene.lights),
+                                                       int(scene.light_px is not None),
+                                                       int(scene.mat_px is not None)))
+
+
+def render_host(scene: Scene, staging: torch.Tensor, out_host: torch.Tensor, stream=None) -> torch.Tensor:
+    """glint_eval_host: host planes in, host image out, copies enqueued on the
+    stream (synchronise before reading out_host)."""
+    H, W = scene.height, scene.width
+    _check_plane(scene.gbuf, "gbuf", (16,), host=True)
+    _check_plane(scene.light_px, "light_px", (H, W, 4), host=True)
+    _check_plane(scene.mat_px, "mat_px", (H, W, 2), host=True)
+    _check_plane(out_host, "out_host", (H, W), host=True)
+    if not staging.is_cuda:
+        raise ValueError("staging must be device memory")
+    frame = _lib.frame_struct(scene.gbuf, scene.light_px, scene.mat_px, len(scene.lights))
+    mat = _lib.material_struct(scene.material)
+    lts = _lib.lights_struct(scene.lights)
+    nbytes = staging.numel() * staging.element_size()
+    with torch.cuda.device(staging.device):
+        rc = _lib.lib().glint_eval_host(C.byref(frame), C.byref(mat), lts, out_host.data_ptr(),
+                                        staging.data_ptr(), nbytes, _stream_handle(stream))
+    _lib.check(rc, "glint_eval_host")
+    return out_host
+
+
+def trace(scene: Scene, pixels, cap: Optional[int] = None, stream=None, material=None, lights=None):
+    """Parity records of the listed flat pixel indices (glint_eval_trace).
+    Returns (pix [n], recs [n, cap]) numpy structured arrays; record slots that
+    were not written hold light = -1."""
+    dev = scene.gbuf.device
+    px = torch.as_tensor(np.asarray(pixels, np.int32), device=dev)
+    n = int(px.numel())
+    lts_list = scene.lights if lights is None else lights
+    if cap is None:
+        cap = max(1, len(lts_list)) * 48 * 64
+    pix = torch.zeros(n * _lib.TRACE_PIX_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    recs = torch.full((n * cap * _lib.TRACE_REC_DTYPE.itemsize,), 0xFF, dtype=torch.uint8, device=dev)
+    frame = _lib.frame_struct(scene.gbuf, scene.light_px, scene.mat_px, len(lts_list))
+    mat = _lib.material_struct(material or scene.material)
+    lts = _lib.lights_struct(lts_list)
+    with torch.cuda.device(dev):
+        rc = _lib.lib().glint_eval_trace(C.byref(frame), C.byref(mat), lts, px.data_ptr(), n, pix.data_ptr(),
+                                         recs.data_ptr(), cap, _stream_handle(stream))
+        _lib.check(rc, "glint_eval_trace")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    p = pix.cpu().numpy().view(_lib.TRACE_PIX_DTYPE)
+    r = recs.cpu().numpy().view(_lib.TRACE_REC_DTYPE).reshape(n, cap)
+    return p, r

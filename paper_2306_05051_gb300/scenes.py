@@ -360,3 +360,61 @@ def plane_sphere_fit(W=512, H=512, target=False, device="cpu") -> Scene:
 def by_name(name: str, **kw) -> Scene:
     return {"plane45": plane45, "grazing_plane": grazing_plane, "sphere_plane": sphere_plane,
             "plane_sphere_fit": plane_sphere_fit}[name](**kw)
+
+
+def random_gbuffer(W=131, H=77, seed=0, n_point=1, n_dir=1, material_plane=True, device="cpu") -> Scene:
+    """Randomised G-buffer for edge-case coverage (not a paper workload):
+    footprint areas log-uniform in [1e-13, 1e-2] uv^2, anisotropy up to 1e4
+    at random orientation, uv in [-100, 100], random normals, tangents, view
+    and light directions (some below the horizon), 4% background pixels,
+    1% zero-area footprints, per-pixel alpha in [0.03, 0.7] and density
+    10^[2, 10] when material_plane is set."""
+    gen = torch.Generator().manual_seed(seed)
+    f64 = torch.float64
+    rnd = lambda *s: torch.rand(*s, generator=gen, dtype=f64)
+    nrm = lambda *s: torch.randn(*s, generator=gen, dtype=f64)
+    area = 10.0 ** (rnd(H, W) * 11.0 - 13.0)
+    ratio = 10.0 ** (rnd(H, W) * 4.0)
+    ang = rnd(H, W) * math.pi
+    a, b = torch.sqrt(area * ratio), torch.sqrt(area / ratio)
+    c, s = torch.cos(ang), torch.sin(ang)
+    rot2 = rnd(H, W) * 2 * math.pi
+    c2, s2 = torch.cos(rot2), torch.sin(rot2)
+    # J = Rot(ang) diag(a, b) Rot(rot2)
+    J00 = c * a * c2 - s * b * s2; J01 = -c * a * s2 - s * b * c2
+    J10 = s * a * c2 + c * b * s2; J11 = -s * a * s2 + c * b * c2
+    zero = rnd(H, W) < 0.01
+    J00, J01, J10, J11 = [torch.where(zero, torch.zeros_like(x), x) for x in (J00, J01, J10, J11)]
+    n = _normalize(nrm(H, W, 3))
+    tg = _normalize(nrm(H, W, 3))
+    wv = _normalize(n + 1.2 * nrm(H, W, 3) * 0.5)
+    g = torch.zeros(H, W, 16, dtype=f64)
+    g[..., 0:2] = rnd(H, W, 2) * 200.0 - 100.0
+    g[..., 2], g[..., 3], g[..., 4], g[..., 5] = J00, J10, J01, J11
+    g[..., 6:9] = n
+    g[..., 9:12] = tg
+    g[..., 12:15] = wv
+    bg = rnd(H, W) < 0.04
+    g[bg] = 0.0
+    lp = []
+    for _ in range(n_point):
+        wl = _normalize(n + nrm(H, W, 3) * 0.6)
+        E = 10.0 ** (rnd(H, W) * 2 - 1)
+        pl = torch.cat([wl, E[..., None]], -1)
+        pl[bg] = 0.0
+        lp.append(pl)
+    lights = [Light(kind=0) for _ in range(n_point)]
+    for k in range(n_dir):
+        d = nrm(3)
+        d[1] = d[1].abs() + 0.3
+        lights.append(Light(kind=1, dir=tuple(float(x) for x in d), intensity=1.5))
+    mat_px = None
+    if material_plane:
+        alpha = rnd(H, W) * 0.67 + 0.03
+        dens = 10.0 ** (rnd(H, W) * 8.0 + 2.0)
+        mat_px = torch.stack([alpha, dens], -1)
+        mat_px[bg] = 0.0
+    light_px = torch.stack(lp, 0) if lp else None
+    mat = Material(ndf=int(seed) % 2, alpha_x=0.25, alpha_y=0.15, ln_density=math.log(1e6), n_lods=12)
+    sc = Scene(f"random{seed}", _f32(g), _f32(light_px), _f32(mat_px), mat, lights)
+    return sc.to(device)

@@ -1,0 +1,175 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+seeded workloads, at sizes the oracle finishes in seconds and, for the
+1080p and 4K frames, on sampled pixels of the full-size launch."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import parity
+from paper_2306_05051_gb300 import glint, scenes
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _render(scene_dev):
+    img = glint.render_scene(scene_dev)
+    torch.cuda.synchronize()
+    return img.cpu().numpy().astype(np.float64)
+
+
+def _summary(name, s):
+    print(f"[{name}] traced records {s['n_rec']}, excused mismatches {s['n_excused']}, "
+          f"pixels over tol {s['over']}, max rel err (matched) {s['max_err_matched']:.3g}")
+
+
+@pytest.mark.parametrize("ndf", [0, 1])
+def test_plane45_full_image(orc, ndf):
+    sc = scenes.plane45(ndf=ndf)
+    img = _render(sc.to(DEV))
+    ref = orc.eval_image(sc)
+    assert np.count_nonzero(ref) > 1000
+    s = parity.check_image(orc, sc, sc.to(DEV), img, ref, sample_trace=600)
+    _summary(f"plane45 ndf={ndf}", s)
+
+
+def test_plane_sphere_fit_full_image(orc):
+    sc = scenes.plane_sphere_fit()
+    img = _render(sc.to(DEV))
+    ref = orc.eval_image(sc)
+    s = parity.check_image(orc, sc, sc.to(DEV), img, ref, sample_trace=600)
+    _summary("plane_sphere_fit 512", s)
+
+
+def test_grazing_plane_1080p_sampled(orc):
+    scd = scenes.grazing_plane(device=DEV)
+    sc = scd.to("cpu")
+    img = _render(scd)
+    rng = np.random.default_rng(2)
+    H, W = sc.height, sc.width
+    fg = np.flatnonzero(sc.gbuf[..., 6:9].abs().sum(-1).reshape(-1).numpy() > 0)
+    top = fg[fg < (H // 3) * W]                            # far rows: K > 1, largest footprints
+    px = np.unique(np.concatenate([rng.choice(fg, 12000, replace=False), rng.choice(top, 4000, replace=False)]))
+    ref = orc.eval_image(sc, px=px.astype(np.int32))
+    s = parity.check_image(orc, sc, scd, img, ref, px=px, sample_trace=300)
+    _summary("grazing_plane 1080p", s)
+    assert max(int(p["K"]) for p in s["opix"]) > 1
+
+
+def test_sphere_plane_4k_sampled(orc):
+    scd = scenes.sphere_plane(device=DEV)
+    sc = scd.to("cpu")
+    img = _render(scd)
+    rng = np.random.default_rng(3)
+    fg = np.flatnonzero(sc.gbuf[..., 6:9].abs().sum(-1).reshape(-1).numpy() > 0)
+    px = np.sort(rng.choice(fg, 16000, replace=False))
+    ref = orc.eval_image(sc, px=px.astype(np.int32))
+    s = parity.check_image(orc, sc, scd, img, ref, px=px, sample_trace=300)
+    _summary("sphere_plane 4K", s)
+
+
+def test_sphere_plane_small_full_image(orc):
+    """The 4K scene's geometry at 480 x 270 (larger footprints): every pixel."""
+    sc = scenes.sphere_plane(480, 270)
+    img = _render(sc.to(DEV))
+    ref = orc.eval_image(sc)
+    s = parity.check_image(orc, sc, sc.to(DEV), img, ref, sample_trace=400)
+    _summary("sphere_plane 480x270", s)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_gbuffer_edge_cases(orc, seed):
+    """Ragged 131 x 77 frame: background, zero-area footprints, anisotropy to
+    1e4 (capped sub-footprints), fractional footprints, areas above the top
+    level, negative uv, lights below the horizon, per-pixel material."""
+    sc = scenes.random_gbuffer(seed=seed)
+    img = _render(sc.to(DEV))
+    ref = orc.eval_image(sc)
+    s = parity.check_image(orc, sc, sc.to(DEV), img, ref, sample_trace=500)
+    _summary(f"random seed {seed}", s)
+    stat = np.array([orc.trace_pixel(sc, int(p), cap=1)[0]["status"] for p in range(0, img.size, 3)])
+    assert (stat == 1).any() and (stat == 2).any() and (stat == 0).any()
+    assert (img[ref == 0] == 0).all()
+
+
+def test_trace_counts_48_evaluations_per_pixel_and_light(orc):
+    sc = scenes.sphere_plane(160, 90)
+    scd = sc.to(DEV)
+    fg = np.flatnonzero(sc.gbuf[..., 6:9].abs().sum(-1).reshape(-1).numpy() > 0)[:64].astype(np.int32)
+    pix, recs = glint.trace(scd, fg, cap=2 * 48 * 8)
+    for k, p in enumerate(fg):
+        op, orecs = orc.trace_pixel(sc, int(p))
+        n_on = len(set(orecs["light"]))
+        assert pix[k]["K"] == op["K"]
+        written = recs[k][recs[k]["light"] >= 0]
+        assert len(written) == 48 * int(op["K"]) * n_on == len(orecs)
+
+
+def test_no_lights_background_only_and_one_pixel(orc):
+    sc = scenes.plane45(32, 16)
+    scd = sc.to(DEV)
+    img = glint.render_scene(scd, lights=[]).cpu().numpy()
+    assert (img == 0).all()
+    bg = scenes.Scene("bg", torch.zeros(5, 7, 16), None, None, scenes.Material(), [scenes.Light(kind=1)])
+    assert (glint.render_scene(bg.to(DEV)).cpu().numpy() == 0).all()
+    one = scenes.Scene("one", sc.gbuf[8:9, 16:17].contiguous(), sc.light_px[:, 8:9, 16:17].contiguous(), None,
+                       sc.material, sc.lights)
+    v = glint.render_scene(one.to(DEV)).cpu().numpy()
+    assert v.shape == (1, 1)
+    assert v[0, 0] == pytest.approx(orc.eval_image(one)[0, 0], rel=1e-4, abs=1e-30)
+
+
+def test_maximum_parameters(orc):
+    """Largest supported rings, LODs, lights and sub-footprints."""
+    sc = scenes.random_gbuffer(97, 41, seed=7, n_point=4, n_dir=4)
+    sc.material = scenes.Material(ndf=1, alpha_x=0.4, alpha_y=0.2, ln_density=math.log(1e6), n_lods=16,
+                                  n_rings=6, lod_factor=2, max_sub=64)
+    img = _render(sc.to(DEV))
+    ref = orc.eval_image(sc)
+    s = parity.check_image(orc, sc, sc.to(DEV), img, ref, sample_trace=200)
+    _summary("max params", s)
+
+
+def test_host_buffer_path_matches_device_path(orc):
+    sc = scenes.sphere_plane(320, 180)
+    scd = sc.to(DEV)
+    dev_img = glint.render_scene(scd).cpu()
+    host = scenes.Scene(sc.name, sc.gbuf.pin_memory(), sc.light_px.pin_memory(), sc.mat_px.pin_memory(),
+                        sc.material, sc.lights)
+    staging = torch.empty(glint.staging_bytes(host), dtype=torch.uint8, device=DEV)
+    out = torch.empty(sc.height, sc.width, dtype=torch.float32).pin_memory()
+    glint.render_host(host, staging, out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, dev_img)
+
+
+def test_side_stream_and_repeatability(orc):
+    sc = scenes.plane45(128, 96)
+    scd = sc.to(DEV)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = glint.render_scene(scd, stream=s)
+    s.synchronize()
+    b = glint.render_scene(scd)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_invalid_device_arguments():
+    from paper_2306_05051_gb300 import _lib
+    sc = scenes.plane45(16, 16)
+    with pytest.raises(_lib.GlintError) as e:      # host tensor where device memory is required
+        fr = _lib.frame_struct(sc.gbuf, sc.light_px, None, 1)
+        out = torch.empty(16, 16, device=DEV)
+        import ctypes as C
+        rc = _lib.lib().glint_eval(C.byref(fr), C.byref(_lib.material_struct(sc.material)),
+                                   _lib.lights_struct(sc.lights), out.data_ptr(), 0)
+        _lib.check(rc, "glint_eval")
+    assert e.value.code == -3
+    g = torch.zeros(16 * 16 * 16 + 1, device=DEV)[1:].view(16, 16, 16)   # 4-byte aligned, not 16
+    with pytest.raises(_lib.GlintError) as e:
+        glint.render(g, sc.light_px.to(DEV), None, sc.material, sc.lights)
+    assert e.value.code == -2
