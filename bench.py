@@ -1,0 +1,284 @@
+"""Benchmark of the glint BRDF path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (one step): the 3840x2160 sphere + ground-plane G-buffer (two point
+lights, per-pixel roughness and flake density, 12 LODs) shaded by
+glint_eval, i.e. the whole per-pixel path.  With N > 1 (torchrun, one rank
+per GPU) every rank shades its own frame of the orbit: weak scaling, no
+collective on the data path.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores on a row sample of the same frame.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "glint-shaded Gpixel/s at 4K (fwd, batched vs plain) + fwd+bwd ms; % of roofline"
+WORKLOAD = "sphere_plane 3840x2160, 2 point lights, per-pixel alpha U[0.05,0.5] and log10 density U[3,9], 12 LODs"
+
+# Algorithmic lane-operations of the method as specified, counted as the
+# minimal FP32 / INT32 operations of each step (see the design notes):
+OPS_PER_PIXEL = 120        # frame, footprint SVD / atan2 / log2, split
+OPS_PER_SUB = 350          # LOD, cell, tetrahedron, 4 grid transforms + simplex, 12 spatial hashes
+OPS_PER_PIXEL_LIGHT = 180  # half-vector, NDF ratio, angular texels + 4 hashes, Fresnel, Smith, shade
+OPS_PER_SUB_LIGHT = 60     # 4 gated-binomial parameter sets (P>=1, mu, sigma, ceil n)
+OPS_PER_EVAL = 11          # one hash word (combine + fmix32) and the gate test
+SMS = 152
+LANES_PER_SM = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1])); mx = max(mx, float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(f) > 4 + k and f[4 + k].lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def census(glint, scene_dev):
+    """Exact work counts of one frame: pixels shaded, sub-footprints,
+    pixel-lights, evaluations (trace kernel with no record capacity)."""
+    n = scene_dev.width * scene_dev.height
+    tot = dict(px=0, sub=0, pl=0, sl=0, evals=0)
+    chunk = 1 << 21
+    for s in range(0, n, chunk):
+        pix, _ = glint.trace(scene_dev, np.arange(s, min(n, s + chunk), dtype=np.int32), cap=0)
+        ok = pix["status"] == 0
+        K = pix["K"][ok].astype(np.int64)
+        nrec = pix["n_rec"][ok].astype(np.int64)
+        lights_on = np.where(K > 0, nrec // (48 * np.maximum(K, 1)), 0)
+        tot["px"] += int(ok.sum()); tot["sub"] += int(K.sum()); tot["pl"] += int(lights_on.sum())
+        tot["sl"] += int((K * lights_on).sum()); tot["evals"] += int(nrec.sum())
+    tot["ops"] = (OPS_PER_PIXEL * tot["px"] + OPS_PER_SUB * tot["sub"] + OPS_PER_PIXEL_LIGHT * tot["pl"]
+                  + OPS_PER_SUB_LIGHT * tot["sl"] + OPS_PER_EVAL * tot["evals"])
+    return tot
+
+
+def frame_bytes(sc):
+    b = sc.gbuf.numel() * 4 + sc.height * sc.width * 4
+    if sc.light_px is not None:
+        b += sc.light_px.numel() * 4
+    if sc.mat_px is not None:
+        b += sc.mat_px.numel() * 4
+    return b
+
+
+def run_ours(args, rank, world, dev):
+    from paper_2306_05051_gb300 import glint, scenes
+    torch.cuda.set_device(dev)
+    scd = scenes.sphere_plane(azimuth_deg=360.0 * rank / max(world, 1), seed=3 + rank, device=dev)
+    npx = scd.width * scd.height
+    out = torch.empty(scd.height, scd.width, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    for _ in range(args.warmup):
+        glint.render_scene(scd, out=out, stream=stream)
+    stream.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            glint.render_scene(scd, out=out, stream=stream)
+        ev1.record(stream)
+        ev1.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_all = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_all = float(t.item())
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    host = scenes.Scene(scd.name, scd.gbuf.cpu().pin_memory(), scd.light_px.cpu().pin_memory(),
+                        scd.mat_px.cpu().pin_memory(), scd.material, scd.lights)
+    staging = torch.empty(glint.staging_bytes(host), dtype=torch.uint8, device=dev)
+    out_host = torch.empty(scd.height, scd.width, dtype=torch.float32).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        glint.render_host(host, staging, out_host, stream=stream)
+    stream.synchronize()
+    e_steps = max(1, min(args.steps, 10))
+    ev0.record(stream)
+    for _ in range(e_steps):
+        glint.render_host(host, staging, out_host, stream=stream)
+    ev1.record(stream)
+    ev1.synchronize()
+    e2e_ms = ev0.elapsed_time(ev1) / e_steps
+    h2d = host.gbuf.numel() * 4 + host.light_px.numel() * 4 + host.mat_px.numel() * 4
+    d2h = npx * 4
+    del staging, host, out_host
+
+    cen = census(glint, scd)
+    return dict(ms=ms_all, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h, npx=npx, census=cen, clocks=clk.summary(),
+                bytes=frame_bytes(scd))
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle on the host cores on a deterministic row sample of the
+    same 4K frame (every 64th row, then further rows until ~seconds)."""
+    import oracle
+    from paper_2306_05051_gb300 import scenes
+    sc = scenes.sphere_plane(device="cpu")
+    W, H = sc.width, sc.height
+    cores = os.cpu_count() or 1
+    rows = [r for phase in range(64) for r in range(phase, H, 64)]     # interleaved, deterministic
+    done, t_used, nrows = 0, 0.0, 0
+    for r in rows:
+        px = np.arange(r * W, (r + 1) * W, dtype=np.int32)
+        t0 = time.perf_counter()
+        oracle.eval_image(sc, px=px, threads=cores)
+        t_used += time.perf_counter() - t0
+        done += W; nrows += 1
+        if t_used >= seconds:
+            break
+    return dict(value=done / t_used / 1e9, unit="Gpixel/s", cores=cores, kind="oracle",
+                sample=f"{nrows} of {H} rows (interleaved by 64) of the 3840x2160 frame, {done} pixels, "
+                       f"{t_used:.1f} s on {cores} threads")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        cb = None
+        for _ in range(args.warmup):
+            cpu_baseline(0.5)
+        for _ in range(args.steps):
+            cb = cpu_baseline(4.0)
+            steps.append(cb["value"])
+        val = statistics.median(steps)
+        cb["value"] = val
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": "Gpixel/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 8294400 / (val * 1e9) * 1e3, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+                          "cpu_baseline": cb,
+                          "e2e": {"value": val, "unit": "Gpixel/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    r = run_ours(args, rank, world, dev)
+    if rank != 0:
+        torch.distributed.destroy_process_group() if world > 1 else None
+        return
+    npx_all = r["npx"] * world
+    value = npx_all / (r["ms"] * 1e-3) / 1e9
+    peaks = _peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = SMS * LANES_PER_SM * mhz * 1e6 / 1e12          # T lane-ops/s
+    cen = r["census"]
+    achieved = cen["ops"] / (r["ms"] * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gpixel/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pixels_per_gpu": r["npx"], "l2": "inputs larger than L2 "
+                   f"({r['bytes'] / 1e6:.0f} MB read+written per step vs 129 MB L2)",
+                   "parallelism": f"replicas x{world} (one frame per GPU)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "T lane-op/s",
+                     "frac": achieved / peak_ops, "traffic": None,
+                     "algorithmic_ops_per_launch": cen["ops"], "evals_per_launch": cen["evals"],
+                     "peak_basis": f"{SMS} SMs x {LANES_PER_SM} FP32/INT32 lanes x {mhz:.0f} MHz",
+                     "hbm_gbs": r["bytes"] / (r["ms"] * 1e-3) / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs")},
+        "e2e": {"value": npx_all / (r["e2e_ms"] * 1e-3) / 1e9, "unit": "Gpixel/s",
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"], "ms_per_step": r["e2e_ms"]},
+        "gpu_launches": args.steps,
+        "clocks": r["clocks"],
+        "census": cen,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

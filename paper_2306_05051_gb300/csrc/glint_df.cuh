@@ -60,6 +60,8 @@ __device__ __forceinline__ df operator+(df a, float b) {
 __device__ __forceinline__ df operator-(df a, float b) { return a + (-b); }
 __device__ __forceinline__ df operator+(float a, df b) { return b + a; }
 __device__ __forceinline__ df operator-(float a, df b) { return (-b) + a; }
+__device__ __forceinline__ df operator*(float a, df b);
+__device__ __forceinline__ df operator/(float a, df b);
 
 __device__ __forceinline__ df operator*(df a, df b) {
     const df c = two_prod(a.hi, b.hi);
@@ -92,6 +94,9 @@ __device__ __forceinline__ df operator/(df a, float b) {
     return fast_two_sum(q1, __fdiv_rn(r, b));
 }
 
+__device__ __forceinline__ df operator*(float a, df b) { return b * a; }
+__device__ __forceinline__ df operator/(float a, df b) { return mkdf(a) / b; }
+
 __device__ __forceinline__ df dfsqrt(df a) {
     if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
     const float s = __fsqrt_rn(a.hi);
@@ -111,14 +116,19 @@ __device__ __forceinline__ bool dfle(df a, float b) { return dfsign(a - b) <= 0;
 __device__ __forceinline__ bool dflt(df a, float b) { return dfsign(a - b) < 0; }
 __device__ __forceinline__ df dfabs(df a) { return dfsign(a) < 0 ? -a : a; }
 
-// floor: integer part (as float, exact) and fraction in [0, 1)
-__device__ __forceinline__ float dffloor(df a, df* frac) {
-    float f = floorf(a.hi);
+// floor: integer part and fraction in [0, 1); requires |a| < 2^31.  The
+// integer is adjusted as an int: above 2^24 a float cannot hold odd integers.
+__device__ __forceinline__ int dffloor(df a, df* frac) {
+    const float f = floorf(a.hi);
     df r = fast_two_sum(__fsub_rn(a.hi, f), a.lo);   // a.hi - f is exact
-    if (dfsign(r) < 0) { f = __fsub_rn(f, 1.0f); r = r + 1.0f; }
-    else if (!dflt(r, 1.0f)) { f = __fadd_rn(f, 1.0f); r = r - 1.0f; }
+    // above 2^24 the low word alone can exceed 1 in magnitude
+    const float g = floorf(r.hi);
+    r = r - g;
+    int i = (int)f + (int)g;
+    if (dfsign(r) < 0) { i -= 1; r = r + 1.0f; }
+    else if (!dflt(r, 1.0f)) { i += 1; r = r - 1.0f; }
     *frac = r;
-    return f;
+    return i;
 }
 
 // Tables and constants built by the host in double precision and split

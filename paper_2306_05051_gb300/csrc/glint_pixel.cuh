@@ -145,25 +145,40 @@ __device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& si
     for (int k = 0; k < 15; ++k) finite &= isfinite(gv[k]);
     if (!finite) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
 
-    // ---- 1. shading frame ------------------------------------------------
-    float n[3] = {g1.z, g1.w, g2.x};
-    if (n[0] == 0.0f && n[1] == 0.0f && n[2] == 0.0f) { sink.pix(1, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
-    float tg[3] = {g2.y, g2.z, g2.w};
-    float wv[3] = {g3.x, g3.y, g3.z};
+    // ---- 1. shading frame (double-float: the angular texel coordinate
+    //      h_t / gamma amplifies FP32 rounding of the frame ~20x) ----------
+    const float nr[3] = {g1.z, g1.w, g2.x};
+    if (nr[0] == 0.0f && nr[1] == 0.0f && nr[2] == 0.0f) { sink.pix(1, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+    const float tr[3] = {g2.y, g2.z, g2.w};
+    const float vr[3] = {g3.x, g3.y, g3.z};
+    df n[3], tg[3], b[3];
     {
-        const float inl = 1.0f / sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-        n[0] *= inl; n[1] *= inl; n[2] *= inl;
+        const df inl = 1.0f / dfsqrt(two_prod(nr[0], nr[0]) + two_prod(nr[1], nr[1]) + two_prod(nr[2], nr[2]));
+        n[0] = inl * nr[0]; n[1] = inl * nr[1]; n[2] = inl * nr[2];
     }
-    const float tn = tg[0] * n[0] + tg[1] * n[1] + tg[2] * n[2];
-    tg[0] -= tn * n[0]; tg[1] -= tn * n[1]; tg[2] -= tn * n[2];
-    const float tl = sqrtf(tg[0] * tg[0] + tg[1] * tg[1] + tg[2] * tg[2]);
-    const float vl = sqrtf(wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2]);
-    if (!(tl > 0.0f) || !(vl > 0.0f)) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
-    tg[0] /= tl; tg[1] /= tl; tg[2] /= tl;
-    wv[0] /= vl; wv[1] /= vl; wv[2] /= vl;
-    const float b[3] = {n[1] * tg[2] - n[2] * tg[1], n[2] * tg[0] - n[0] * tg[2], n[0] * tg[1] - n[1] * tg[0]};
-    const float cos_v = wv[0] * n[0] + wv[1] * n[1] + wv[2] * n[2];
-    if (!(cos_v > 0.0f)) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+    const df tn = n[0] * tr[0] + n[1] * tr[1] + n[2] * tr[2];
+    df tp[3] = {tr[0] - tn * n[0], tr[1] - tn * n[1], tr[2] - tn * n[2]};
+    const df tl2 = tp[0] * tp[0] + tp[1] * tp[1] + tp[2] * tp[2];
+    const df vl2 = two_prod(vr[0], vr[0]) + two_prod(vr[1], vr[1]) + two_prod(vr[2], vr[2]);
+    if (!(tl2.hi > 0.0f) || !(vl2.hi > 0.0f)) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+    {
+        const df itl = 1.0f / dfsqrt(tl2);
+        tg[0] = tp[0] * itl; tg[1] = tp[1] * itl; tg[2] = tp[2] * itl;
+    }
+    b[0] = n[1] * tg[2] - n[2] * tg[1];
+    b[1] = n[2] * tg[0] - n[0] * tg[2];
+    b[2] = n[0] * tg[1] - n[1] * tg[0];
+    // view direction in the local frame (t, b, n), unit length
+    df wv[3];
+    {
+        const df ivl = 1.0f / dfsqrt(vl2);
+        const df x = tg[0] * vr[0] + tg[1] * vr[1] + tg[2] * vr[2];
+        const df y = b[0] * vr[0] + b[1] * vr[1] + b[2] * vr[2];
+        const df z = n[0] * vr[0] + n[1] * vr[1] + n[2] * vr[2];
+        wv[0] = x * ivl; wv[1] = y * ivl; wv[2] = z * ivl;
+    }
+    if (dfsign(wv[2]) <= 0) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+    const float cos_v = wv[2].hi;
 
     float ax = P.ax, ay = P.ay;
     df rho = ldf(P.rho), srho = ldf(P.sqrt_rho);
@@ -199,17 +214,28 @@ __device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& si
     df phi = scale2(dfatan2(scale2(F, 1), E - G, T.d), -1);
     if (dfsign(phi) < 0) phi = phi + ldf(T.d.pi);
     if (!dflt(phi, ldf(T.d.pi))) phi = phi - ldf(T.d.pi);
-    const float s0f = sqrtf(s0sq.hi) * pow2f(je);
-    const float s1f = Pft.hi / s0f;
+    // major axis u0 of the footprint (eigenvector of J J^T for sigma0^2),
+    // oriented like (cos phi, sin phi) with phi in [0, pi)
+    df u0x, u0y;
+    {
+        df ex, ey;
+        if (dfsign(hm) >= 0) { ex = hyp + hm; ey = F; } else { ex = F; ey = hyp - hm; }
+        if (ex.hi == 0.0f && ey.hi == 0.0f) ex = mkdf(1.0f);
+        const df inv = 1.0f / dfsqrt(ex * ex + ey * ey);
+        u0x = ex * inv; u0y = ey * inv;
+        if (dfsign(u0y) < 0 || (dfsign(u0y) == 0 && dfsign(u0x) < 0)) { u0x = -u0x; u0y = -u0y; }
+    }
+    const df sig0 = scale2(dfsqrt(s0sq), je);
+    const df sig1 = Pft / sig0;
 
     // ---- 3. sub-footprints --------------------------------------------
     int Kmaj = 1;
     const df rq = scale2(ratio, -P.M);
     if (dfsign(rq - 1.0f) > 0) {
         df fr;
-        float c = dffloor(rq, &fr);
-        if (dfsign(fr) > 0) c += 1.0f;
-        Kmaj = c >= (float)P.Kmax ? P.Kmax : (int)c;
+        int c = dffloor(rq, &fr);           // rq <= 2^19 (ratio capped at 2^20)
+        if (dfsign(fr) > 0) c += 1;
+        Kmaj = c >= P.Kmax ? P.Kmax : c;
     }
     const df Ap = A / (float)Kmaj;
     int ksub = 1;
@@ -239,12 +265,12 @@ __device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& si
     if (dfsign(rr) < 0) rr = mkdf(0.0f);
     if (!dflt(rr, (float)P.M)) rr = mkdf((float)P.M);
     df fx_unused;
-    int m = (int)dffloor(rr, &fx_unused);
+    int m = dffloor(rr, &fx_unused);
     if (m > P.M - 1) m = P.M - 1;
     const df x = rr - (float)m;
     const int nm = m == 0 ? 4 : (1 << (m + 1));
     df t;
-    int a = (int)dffloor(scale2(phi * ldf(T.d.inv_pi), m == 0 ? 2 : m + 1), &t);
+    int a = dffloor(scale2(phi * ldf(T.d.inv_pi), m == 0 ? 2 : m + 1), &t);
     a %= nm;
     Vert tv[3];
     df lam[3];
@@ -307,44 +333,53 @@ __device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& si
     constexpr int NLA = NLT > 0 ? NLT : kMaxLights;
     LightState ls[NLA];
     const float Dn = 1.0f / (3.14159265358979f * ax * ay);
-    const float lam_v = smith_lambda(P.ndf, ax, ay, wv[0] * tg[0] + wv[1] * tg[1] + wv[2] * tg[2],
-                                     wv[0] * b[0] + wv[1] * b[1] + wv[2] * b[2], cos_v);
+    const float lam_v = smith_lambda(P.ndf, ax, ay, wv[0].hi, wv[1].hi, cos_v);
 #pragma unroll
     for (int l = 0; l < NLA; ++l) {
         LightState& L = ls[l];
         L.on = false;
         if (l >= nL) continue;
         const KLight kl = P.lights[l];
-        float wl[3], E;
+        float lr[3], E;
         if (kl.kind == 0) {
             const float4 lp = __ldg(P.light_px + (size_t)l * P.npx + px);
-            wl[0] = lp.x; wl[1] = lp.y; wl[2] = lp.z; E = lp.w;
+            lr[0] = lp.x; lr[1] = lp.y; lr[2] = lp.z; E = lp.w;
         } else {
-            wl[0] = kl.dx; wl[1] = kl.dy; wl[2] = kl.dz; E = kl.E;
+            lr[0] = kl.dx; lr[1] = kl.dy; lr[2] = kl.dz; E = kl.E;
         }
-        const float wll = sqrtf(wl[0] * wl[0] + wl[1] * wl[1] + wl[2] * wl[2]);
-        if (!(wll > 0.0f)) continue;
-        wl[0] /= wll; wl[1] /= wll; wl[2] /= wll;
-        const float cos_l = wl[0] * n[0] + wl[1] * n[1] + wl[2] * n[2];
-        if (!(cos_l > 0.0f)) continue;
-        float h[3] = {wv[0] + wl[0], wv[1] + wl[1], wv[2] + wl[2]};
-        const float hl = sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
-        h[0] /= hl; h[1] /= hl; h[2] /= hl;
-        const float ht = h[0] * tg[0] + h[1] * tg[1] + h[2] * tg[2];
-        const float hb = h[0] * b[0] + h[1] * b[1] + h[2] * b[2];
-        const float hn = h[0] * n[0] + h[1] * n[1] + h[2] * n[2];
+        const df ll2 = two_prod(lr[0], lr[0]) + two_prod(lr[1], lr[1]) + two_prod(lr[2], lr[2]);
+        if (!(ll2.hi > 0.0f)) continue;
+        // light direction in the local frame, unit length
+        df wl[3];
+        {
+            const df il = 1.0f / dfsqrt(ll2);
+            wl[0] = (tg[0] * lr[0] + tg[1] * lr[1] + tg[2] * lr[2]) * il;
+            wl[1] = (b[0] * lr[0] + b[1] * lr[1] + b[2] * lr[2]) * il;
+            wl[2] = (n[0] * lr[0] + n[1] * lr[1] + n[2] * lr[2]) * il;
+        }
+        if (dfsign(wl[2]) <= 0) continue;
+        const float cos_l = wl[2].hi;
+        df h[3] = {wv[0] + wl[0], wv[1] + wl[1], wv[2] + wl[2]};
+        {
+            const df ih = 1.0f / dfsqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+            h[0] = h[0] * ih; h[1] = h[1] * ih; h[2] = h[2] * ih;
+        }
+        const float ht = h[0].hi, hb = h[1].hi, hn = h[2].hi;
         // Eq. 4: p = R D(h) / D(n)
         const float e = (ht / ax) * (ht / ax) + (hb / ay) * (hb / ay);
         const float hn2 = hn * hn;
         const float rat = P.ndf == 0 ? expf(-e / hn2) / (hn2 * hn2) : 1.0f / ((e + hn2) * (e + hn2));
         L.p = fminf(P.R * rat, 1.0f);
-        // Eq. 14: bilinear angular texels of the projected half-vector
-        const float afx = ht / P.gamma, afy = hb / P.gamma;
-        const float fax = floorf(afx), fay = floorf(afy);
-        const float fx = afx - fax, fy = afy - fay;
-        const int ix = (int)fax, iy = (int)fay;
-        L.v[0] = (1.0f - fx) * (1.0f - fy); L.v[1] = fx * (1.0f - fy);
-        L.v[2] = (1.0f - fx) * fy;          L.v[3] = fx * fy;
+        // Eq. 14: bilinear angular texels of the projected half-vector; the
+        // weights are formed from double-float fractions so each keeps full
+        // relative precision however small it is.
+        df fxd, fyd;
+        const int ix = dffloor(h[0] / P.gamma, &fxd);
+        const int iy = dffloor(h[1] / P.gamma, &fyd);
+        const float fx = fxd.hi, fy = fyd.hi;
+        const float gx = (1.0f - fxd).hi, gy = (1.0f - fyd).hi;
+        L.v[0] = gx * gy; L.v[1] = fx * gy;
+        L.v[2] = gx * fy; L.v[3] = fx * fy;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             L.ax[k] = ix + (k & 1); L.ay[k] = iy + (k >> 1);
@@ -353,11 +388,10 @@ __device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& si
             L.A0[k] = hx; L.A1[k] = hy;
         }
         // Eq. 2 with D_P = D(n)/R C/A: out_l = F G D(n) E / (4 R cos_v) * C / A
-        const float vh = wv[0] * h[0] + wv[1] * h[1] + wv[2] * h[2];
+        const float vh = wv[0].hi * ht + wv[1].hi * hb + cos_v * hn;
         const float om = 1.0f - vh;
         const float Fr = P.F0 + (1.0f - P.F0) * (om * om) * (om * om) * om;
-        const float lam_l = smith_lambda(P.ndf, ax, ay, wl[0] * tg[0] + wl[1] * tg[1] + wl[2] * tg[2],
-                                         wl[0] * b[0] + wl[1] * b[1] + wl[2] * b[2], cos_l);
+        const float lam_l = smith_lambda(P.ndf, ax, ay, wl[0].hi, wl[1].hi, cos_l);
         const float Gs = 1.0f / ((1.0f + lam_v) * (1.0f + lam_l));
         L.shade = Fr * Gs * Dn * E / (4.0f * P.R * cos_v);
         L.on = true;
@@ -368,16 +402,18 @@ __device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& si
 #pragma unroll
     for (int l = 0; l < NLA; ++l) C[l] = 0.0f;
     const int ncols = Kmaj * ksub;
-    float sph, cph;
-    sincosf(phi.hi, &sph, &cph);
-    const float u0 = g0.x, v0 = g0.y;
     int status = 0;
     for (int sub = 0; sub < K && status == 0; ++sub) {
-        const int ia = sub % ncols, ib = sub / ncols;
-        const float oa = ((float)ia + 0.5f) / (float)ncols - 0.5f;
-        const float ob = ((float)ib + 0.5f) / (float)ksub - 0.5f;
-        const df us = two_sum(u0, s0f * oa * cph - s1f * ob * sph);
-        const df vs = two_sum(v0, s0f * oa * sph + s1f * ob * cph);
+        df us = mkdf(g0.x), vs = mkdf(g0.y);
+        if (K > 1) {
+            // centre of sub-rectangle (ia, ib) of the sigma0 x sigma1 rectangle
+            // aligned with (u0, u1 = (-u0y, u0x))
+            const int ia = sub % ncols, ib = sub / ncols;
+            const df oa = sig0 * (mkdf((float)(2 * ia + 1 - ncols)) / (float)(2 * ncols));
+            const df ob = sig1 * (mkdf((float)(2 * ib + 1 - ksub)) / (float)(2 * ksub));
+            us = us + (oa * u0x - ob * u0y);
+            vs = vs + (oa * u0y + ob * u0x);
+        }
         uint32_t S0[4][3], S1[4][3];
         float uw[4][3];
         int32_t li[4][3], lj[4][3];
@@ -394,17 +430,17 @@ __device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& si
             const df qy = sl * (df{Q.r1.x, Q.r1.y} * us + df{Q.r1.z, Q.r1.w} * vs);
             if (!(fabsf(qx.hi) < 1073741824.0f) || !(fabsf(qy.hi) < 1073741824.0f)) { status = 3; break; }
             df fxd, fyd;
-            const int i0 = (int)dffloor(qx, &fxd);
-            const int j0 = (int)dffloor(qy, &fyd);
-            const float fx = fxd.hi, fy = fyd.hi;
+            const int i0 = dffloor(qx, &fxd);
+            const int j0 = dffloor(qy, &fyd);
+            // barycentric weights from double-float fractions (full relative precision)
             if (!dflt(fxd, fyd)) {
-                li[i][0] = i0;     lj[i][0] = j0;     uw[i][0] = 1.0f - fx;
-                li[i][1] = i0 + 1; lj[i][1] = j0;     uw[i][1] = fx - fy;
-                li[i][2] = i0 + 1; lj[i][2] = j0 + 1; uw[i][2] = fy;
+                li[i][0] = i0;     lj[i][0] = j0;     uw[i][0] = (1.0f - fxd).hi;
+                li[i][1] = i0 + 1; lj[i][1] = j0;     uw[i][1] = (fxd - fyd).hi;
+                li[i][2] = i0 + 1; lj[i][2] = j0 + 1; uw[i][2] = fyd.hi;
             } else {
-                li[i][0] = i0;     lj[i][0] = j0;     uw[i][0] = 1.0f - fy;
-                li[i][1] = i0;     lj[i][1] = j0 + 1; uw[i][1] = fy - fx;
-                li[i][2] = i0 + 1; lj[i][2] = j0 + 1; uw[i][2] = fx;
+                li[i][0] = i0;     lj[i][0] = j0;     uw[i][0] = (1.0f - fyd).hi;
+                li[i][1] = i0;     lj[i][1] = j0 + 1; uw[i][1] = (fyd - fxd).hi;
+                li[i][2] = i0 + 1; lj[i][2] = j0 + 1; uw[i][2] = fxd.hi;
             }
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
