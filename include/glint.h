@@ -142,11 +142,12 @@ int glint_eval_host(const GlintFrame* host_frame, const GlintMaterial* material,
  *   px:   device, n_px int32 flat pixel indices.
  *   pix:  device, n_px records.
  *   recs: device, n_px * rec_cap records; pixel k owns recs[k*rec_cap ...];
- *         records beyond rec_cap are not written (pix.n_rec holds the total). */
+ *         records whose canonical index is >= rec_cap are not written; slots
+ *         of lights facing away from the surface are left untouched. */
 typedef struct GlintTracePix {
     int32_t status;          /* 0 shaded, 1 background, 2 invalid, 3 lattice out of range */
     int32_t K;               /* sub-footprints */
-    int32_t n_rec;           /* records produced (may exceed rec_cap) */
+    int32_t n_rec;           /* evaluation records produced (lights facing away produce none) */
     int32_t pad;
     float   A, r, phi, out;  /* flakes in footprint, ratio, orientation, radiance */
 } GlintTracePix;

@@ -60,8 +60,6 @@ __device__ __forceinline__ df operator+(df a, float b) {
 __device__ __forceinline__ df operator-(df a, float b) { return a + (-b); }
 __device__ __forceinline__ df operator+(float a, df b) { return b + a; }
 __device__ __forceinline__ df operator-(float a, df b) { return (-b) + a; }
-__device__ __forceinline__ df operator*(float a, df b);
-__device__ __forceinline__ df operator/(float a, df b);
 
 __device__ __forceinline__ df operator*(df a, df b) {
     const df c = two_prod(a.hi, b.hi);
@@ -80,28 +78,47 @@ __device__ __forceinline__ df scale2(df a, int e) {
     return {__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)};
 }
 
+// Approximate reciprocal (MUFU, about 2 ulp).  Every division below uses it
+// for a first quotient and then corrects with an exactly computed residual,
+// so the double-float result does not depend on the reciprocal's last bits.
+__device__ __forceinline__ float approx_rcp(float x) { return __fdividef(1.0f, x); }
+
 __device__ __forceinline__ df operator/(df a, df b) {
-    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const float ib = approx_rcp(b.hi);
+    const float q1 = __fmul_rn(a.hi, ib);
     const df r = a - b * q1;
-    const float q2 = __fdiv_rn(r.hi, b.hi);
-    return fast_two_sum(q1, q2);
+    return fast_two_sum(q1, __fmul_rn(r.hi, ib));
 }
 
-__device__ __forceinline__ df operator/(df a, float b) {
-    const float q1 = __fdiv_rn(a.hi, b);
+// a / b for a float b with ib ~ 1/b
+__device__ __forceinline__ df div_by(df a, float b, float ib) {
+    const float q1 = __fmul_rn(a.hi, ib);
     const df p = two_prod(q1, b);
     const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), a.lo);
-    return fast_two_sum(q1, __fdiv_rn(r, b));
+    return fast_two_sum(q1, __fmul_rn(r, ib));
 }
+__device__ __forceinline__ df operator/(df a, float b) { return div_by(a, b, approx_rcp(b)); }
+__device__ __forceinline__ df A_over(df a, int k) { return div_by(a, (float)k, approx_rcp((float)k)); }
 
 __device__ __forceinline__ df operator*(float a, df b) { return b * a; }
 __device__ __forceinline__ df operator/(float a, df b) { return mkdf(a) / b; }
 
+// sqrt(a), a >= 0: approximate root, then one correction with the exact residual
 __device__ __forceinline__ df dfsqrt(df a) {
     if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
-    const float s = __fsqrt_rn(a.hi);
+    const float r = rsqrtf(a.hi);
+    const float s = __fmul_rn(a.hi, r);
     const float e = __fadd_rn(__fmaf_rn(-s, s, a.hi), a.lo);
-    return fast_two_sum(s, __fmul_rn(e, __fdiv_rn(0.5f, s)));
+    return fast_two_sum(s, __fmul_rn(e, __fmul_rn(0.5f, r)));
+}
+
+// 1 / sqrt(a), a > 0: approximate value y, then y + y (1 - a y^2) / 2 with
+// a y^2 evaluated in double-float
+__device__ __forceinline__ df dfrsqrt(df a) {
+    const float y = rsqrtf(a.hi);
+    const df ay2 = a * two_prod(y, y);
+    const df e = 1.0f - ay2;
+    return fast_two_sum(y, __fmul_rn(__fmul_rn(y, e.hi), 0.5f));
 }
 
 // sign of a normalised double-float: -1, 0, +1

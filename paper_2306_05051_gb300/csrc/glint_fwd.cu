@@ -1,7 +1,29 @@
 // Plain forward kernel (one frame) and the parity-trace kernel.
+//
+// Forward kernel mapping: one warp shades 32 consecutive pixels (lane =
+// pixel) for the per-pixel, per-light and per-sub-footprint setup, then walks
+// the evaluations in a warp-uniform loop (sub-footprint, light, 4 grids x 3
+// simplex vertices x 4 angular texels).  Each lane tests its gate with one
+// hash word; the rare open gates (their count needs the second word, a normal
+// quantile and the floor) are appended to a per-warp queue in shared memory
+// and evaluated 32 at a time at full warp width, so that the divergent,
+// expensive part of the binomial law costs one lane-slot per open gate
+// rather than a warp-slot.  Results are returned to their owner lanes in
+// enqueue order, so the image is deterministic.
 #include "glint_kernels.cuh"
 
 namespace glint {
+
+constexpr int kWarpsPerBlock = 8;
+constexpr int kQ = 64;                    // queue capacity per warp (ring)
+
+struct WarpQueue {
+    uint32_t word[kQ];                    // pre-image of the second hash word
+    float mu[kQ], sig[kQ], nceil[kQ], w[kQ];
+    int32_t owner[kQ];
+    float res[32];
+    uint32_t mask[32];
+};
 
 // Copy the double-float tables (only the rotation entries up to ring M)
 // from the parameter block into shared memory.
@@ -13,39 +35,184 @@ __device__ __forceinline__ void load_tables(const KParams& P, Tables& T) {
     __syncthreads();
 }
 
-template <int NLT>
+// Evaluate the n <= 32 queue entries starting at `head`: lane k takes entry
+// head + k.  Each owner lane then adds its entries' values in queue order.
+__device__ __noinline__ void flush_queue(WarpQueue& q, int head, int n, float& acc) {
+    const int lane = threadIdx.x & 31;
+    const int e = (head + lane) & (kQ - 1);
+    float val = 0.0f;
+    int owner = 32 + lane;                       // unique dummy for empty slots
+    if (lane < n) {
+        float cc;
+        val = q.w[e] * open_count(fmix32(q.word[e]), q.mu[e], q.sig[e], q.nceil[e], &cc);
+        owner = q.owner[e];
+    }
+    q.res[lane] = val;
+    q.mask[lane] = 0u;
+    __syncwarp();
+    const unsigned grp = __match_any_sync(0xffffffffu, owner);
+    if (lane < n && lane == __ffs(grp) - 1) q.mask[owner] = grp;
+    __syncwarp();
+    unsigned mine = q.mask[lane];
+    while (mine) {
+        const int k = __ffs(mine) - 1;
+        acc += q.res[k];
+        mine &= mine - 1;
+    }
+    __syncwarp();
+}
+
+struct LightEval {          // what the evaluation loop needs of one light
+    bool on;
+    float p, shade;
+    float v[4];
+    uint32_t A0[4], A1[4];
+};
+
+// Shade the pixel of this lane (px valid or not); all 32 lanes call together.
+__device__ float shade_warp(const KParams& P, const Tables& T, WarpQueue& q, int px, bool valid) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    PixelSetup S;
+    S.status = 1;
+    S.K = 0;
+    if (valid) setup_pixel(P, T, px, S);
+    LightState ls[kMaxLights];
+    for (int l = 0; l < P.nL; ++l) {
+        ls[l].on = false;
+        if (S.status == 0) setup_light(P, S, px, l, ls[l]);
+    }
+    const int K = S.status == 0 ? S.K : 0;
+    const int Kw = __reduce_max_sync(0xffffffffu, K);
+    float acc = 0.0f;
+    int head = 0, count = 0;                     // warp-uniform queue state
+    bool in_range = true;
+    for (int sub = 0; sub < Kw; ++sub) {
+        SubState U;
+        bool act = sub < K && in_range;
+        if (act) {
+            in_range = setup_sub(P, T, S, sub, U);
+            act = in_range;
+        }
+#pragma unroll 1
+        for (int l = 0; l < P.nL; ++l) {
+            LightEval L;
+            L.on = act && ls[l].on;
+            L.p = ls[l].p; L.shade = ls[l].shade;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { L.v[k] = ls[l].v[k]; L.A0[k] = ls[l].A0[k]; L.A1[k] = ls[l].A1[k]; }
+            if (!__any_sync(0xffffffffu, L.on)) continue;
+#pragma unroll 1
+            for (int i = 0; i < 4; ++i) {
+                CountLaw law = count_law(S.ntr[i], L.p);
+                if (!L.on) law.Tg = 0u;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const uint32_t s0 = U.S0[3 * i + j], s1 = U.S1[3 * i + j];
+                    const float uw = U.uw[3 * i + j] * L.shade;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const bool g = gate_open(fmix32(s0 + L.A0[k]), law.Tg);
+                        const unsigned m = __ballot_sync(0xffffffffu, g);
+                        if (m) {
+                            if (g) {
+                                const int pos = (head + count + __popc(m & lt_mask)) & (kQ - 1);
+                                q.word[pos] = s1 + L.A1[k];
+                                q.mu[pos] = law.mu; q.sig[pos] = law.sig; q.nceil[pos] = law.nceil;
+                                q.w[pos] = uw * L.v[k];
+                                q.owner[pos] = lane;
+                            }
+                            count += __popc(m);
+                            if (count >= 32) {
+                                __syncwarp();
+                                flush_queue(q, head, 32, acc);
+                                head = (head + 32) & (kQ - 1);
+                                count -= 32;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (count > 0) {
+        __syncwarp();
+        flush_queue(q, head, count, acc);
+    }
+    if (S.status != 0 || !in_range) return 0.0f;
+    return acc / S.A.hi;
+}
+
 __global__ void __launch_bounds__(256) fwd_kernel(const __grid_constant__ KParams P) {
     __shared__ Tables T;
+    __shared__ WarpQueue Qs[kWarpsPerBlock];
     load_tables(P, T);
-    const int stride = gridDim.x * blockDim.x;
-    for (int px = blockIdx.x * blockDim.x + threadIdx.x; px < P.npx; px += stride) {
-        NoSink s;
-        P.out[px] = shade_pixel<NLT>(P, T, px, s);
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpQueue& q = Qs[wib];
+    const int nw = gridDim.x * kWarpsPerBlock;
+    for (int base = (blockIdx.x * kWarpsPerBlock + wib) * 32; base < P.npx; base += nw * 32) {
+        const int px = base + lane;
+        const float o = shade_warp(P, T, q, px, px < P.npx);
+        if (px < P.npx) P.out[px] = o;
     }
 }
 
-struct TraceSink {
-    static constexpr bool kTrace = true;
-    GlintTracePix* pixrec;
-    GlintTraceRec* recs;
-    int cap;
-    int nmax;
-    __device__ void pix(int status, int K, float A, float r, float phi, float out) {
-        pixrec->status = status; pixrec->K = K; pixrec->A = A; pixrec->r = r; pixrec->phi = phi;
-        pixrec->out = out; pixrec->n_rec = nmax; pixrec->pad = 0;
+// --------------------------------------------------------------------------
+// parity trace: one thread per listed pixel, every evaluation recorded
+// --------------------------------------------------------------------------
+__device__ void trace_pixel(const KParams& P, const Tables& T, int px, GlintTracePix* pr, GlintTraceRec* recs,
+                            int cap) {
+    PixelSetup S;
+    setup_pixel(P, T, px, S);
+    pr->status = S.status; pr->K = S.status == 0 ? S.K : 0; pr->n_rec = 0; pr->pad = 0;
+    pr->A = S.status == 0 ? S.A.hi : 0.0f; pr->r = S.status == 0 ? S.ratio.hi : 0.0f;
+    pr->phi = S.status == 0 ? S.phi.hi : 0.0f; pr->out = 0.0f;
+    if (S.status != 0) return;
+    LightState ls[kMaxLights];
+    for (int l = 0; l < P.nL; ++l) setup_light(P, S, px, l, ls[l]);
+    float C[kMaxLights];
+    for (int l = 0; l < P.nL; ++l) C[l] = 0.0f;
+    int nrec = 0;
+    for (int sub = 0; sub < S.K; ++sub) {
+        SubState U;
+        if (!setup_sub(P, T, S, sub, U)) { pr->status = 3; pr->n_rec = nrec; return; }
+        for (int l = 0; l < P.nL; ++l) {
+            const LightState& L = ls[l];
+            if (!L.on) continue;
+            for (int i = 0; i < 4; ++i) {
+                const CountLaw law = count_law(S.ntr[i], L.p);
+                for (int j = 0; j < 3; ++j) {
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t h0 = fmix32(U.S0[3 * i + j] + L.A0[k]);
+                        const uint32_t h1 = fmix32(U.S1[3 * i + j] + L.A1[k]);
+                        const bool g = gate_open(h0, law.Tg);
+                        float c = 0.0f, cc = 0.0f;
+                        if (g) {
+                            c = open_count(h1, law.mu, law.sig, law.nceil, &cc);
+                            C[l] += U.uw[3 * i + j] * L.v[k] * c;
+                        }
+                        const int idx = (((l * S.K + sub) * 4 + i) * 3 + j) * 4 + k;
+                        ++nrec;
+                        if (idx < cap) {
+                            GlintTraceRec& R = recs[idx];
+                            R.light = l; R.sub = sub; R.vert = i; R.sv = j; R.av = k; R.grid_id = U.gid[i];
+                            R.i = U.li[3 * i + j]; R.j = U.lj[3 * i + j]; R.ax = L.ax[k]; R.ay = L.ay[k];
+                            R.h0 = h0; R.h1 = h1; R.gate = g ? 1 : 0;
+                            R.c = c < 2147483647.0f ? (int)c : 2147483647;
+                            R.n = S.ntr[i]; R.P1 = law.P1; R.mu = law.mu; R.sigma = law.sig; R.c_cont = cc;
+                            R.u = U.uw[3 * i + j]; R.v = L.v[k]; R.p = L.p;
+                        }
+                    }
+                }
+            }
+        }
     }
-    __device__ void rec(int idx, int light, int sub, int vert, int sv, int av, uint32_t gid, int i, int j,
-                        int ax, int ay, uint32_t h0, uint32_t h1, int gate, int c, float n, float P1,
-                        float mu, float sigma, float cc, float u, float v, float p) {
-        nmax = idx + 1 > nmax ? idx + 1 : nmax;
-        pixrec->n_rec = nmax;
-        if (idx >= cap) return;
-        GlintTraceRec& R = recs[idx];
-        R.light = light; R.sub = sub; R.vert = vert; R.sv = sv; R.av = av; R.grid_id = gid;
-        R.i = i; R.j = j; R.ax = ax; R.ay = ay; R.h0 = h0; R.h1 = h1; R.gate = gate; R.c = c;
-        R.n = n; R.P1 = P1; R.mu = mu; R.sigma = sigma; R.c_cont = cc; R.u = u; R.v = v; R.p = p;
-    }
-};
+    float out = 0.0f;
+    for (int l = 0; l < P.nL; ++l)
+        if (ls[l].on) out += ls[l].shade * C[l];
+    pr->out = out / S.A.hi;
+    pr->n_rec = nrec;
+}
 
 __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ KParams P, const int32_t* px_list,
                                                     int32_t n_px, GlintTracePix* pix, GlintTraceRec* recs,
@@ -55,15 +222,16 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ KPar
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_px) return;
     const int px = px_list[k];
-    TraceSink s{pix + k, recs + (size_t)k * cap, cap, 0};
-    if (px < 0 || px >= P.npx) { s.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return; }
-    shade_pixel<0>(P, T, px, s);
+    if (px < 0 || px >= P.npx) {
+        pix[k].status = 2; pix[k].K = 0; pix[k].n_rec = 0; pix[k].pad = 0;
+        pix[k].A = pix[k].r = pix[k].phi = pix[k].out = 0.0f;
+        return;
+    }
+    trace_pixel(P, T, px, pix + k, recs + (size_t)k * cap, cap);
 }
 
 cudaError_t launch_fwd(const KParams& P, cudaStream_t s, FwdLaunch cfg) {
-    if (P.nL == 1) fwd_kernel<1><<<cfg.blocks, cfg.threads, 0, s>>>(P);
-    else if (P.nL == 2) fwd_kernel<2><<<cfg.blocks, cfg.threads, 0, s>>>(P);
-    else fwd_kernel<0><<<cfg.blocks, cfg.threads, 0, s>>>(P);
+    fwd_kernel<<<cfg.blocks, cfg.threads, 0, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -1,19 +1,23 @@
 // Per-pixel glint BRDF evaluation (device code), Deliot & Belcour 2023.
 //
 // One pixel, in the paper's order:
-//   1. shading frame from the G-buffer                         (Sec. 3)
-//   2. footprint: SVD of dUV/d(x,y) -> area, ratio, orientation (Sec. 5.1)
-//   3. sub-footprints when the ratio or area leaves the grids   (Sec. 4.2 ext.)
-//   4. LOD bracket with area-linear coordinate                   (Sec. 5.2, Eq. 13)
+//   1. shading frame from the G-buffer                          (Sec. 3)
+//   2. footprint: SVD of dUV/d(x,y) -> area, ratio, orientation  (Sec. 5.1)
+//   3. sub-footprints when the ratio or area leaves the grids    (Sec. 4.2 ext.)
+//   4. LOD bracket with area-linear coordinate                    (Sec. 5.2, Eq. 13)
 //   5. ratio/orientation cell, pentagon triangle, prism tetrahedron
-//      -> 4 grids with trials w_i f^l_i                          (Fig. 5, Sec. 6.1)
+//      -> 4 grids with trials w_i f^l_i                           (Fig. 5, Sec. 6.1)
 //   6. per grid: anisotropic transform + simplex lattice -> 3 texels (Eq. 12, Sec. 6.2)
 //   7. per light: NDF ratio p, angular texels (4), hash, gated
 //      binomial counts (48 per light), interpolation of realisations
-//                                                                (Eq. 4, Eq. 14, Sec. 6.3)
-//   8. D_P = D(n)/R * C / A and the microfacet BRDF             (Eq. 2-3)
-// Steps 2-6 run in double-float (see glint_df.cuh), the per-light and
-// per-evaluation work in FP32 and 32-bit integers.
+//                                                                 (Eq. 4, Eq. 14, Sec. 6.3)
+//   8. D_P = D(n)/R * C / A and the microfacet BRDF              (Eq. 2-3)
+// Steps 1-6 and the angular coordinate run in double-float (see
+// glint_df.cuh); p, the count parameters and the per-evaluation work run in
+// FP32 and 32-bit integers.
+//
+// The pieces below are shared by the image kernels (warp-cooperative, see
+// glint_fwd.cu) and the per-thread parity-trace kernel.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -102,6 +106,36 @@ __device__ __forceinline__ float normal_of_word(uint32_t h) {
 }
 
 // --------------------------------------------------------------------------
+// gated Gaussian binomial (Sec. 6.3)
+// --------------------------------------------------------------------------
+struct CountLaw {
+    uint32_t Tg;      // gate threshold: theta0 < P>=1  <=>  ((h0 >> 7) | 1) < Tg
+    float P1, mu, sig, nceil;
+};
+
+__device__ __forceinline__ CountLaw count_law(float n, float p) {
+    CountLaw c;
+    c.P1 = 0.0f;
+    if (n > 0.0f && p > 0.0f) c.P1 = p >= 1.0f ? 1.0f : -expm1f(n * log1pf(-p));
+    c.Tg = (uint32_t)ceilf(c.P1 * 33554432.0f);            // 2^25
+    const float nm1 = n > 1.0f ? n - 1.0f : 0.0f;
+    c.mu = nm1 * p;
+    const float var = c.mu * (1.0f - p);
+    c.sig = var > 0.0f ? sqrtf(var) : 0.0f;
+    c.nceil = ceilf(n);
+    return c;
+}
+
+__device__ __forceinline__ bool gate_open(uint32_t h0, uint32_t Tg) { return ((h0 >> 7) | 1u) < Tg; }
+
+// Count of an open gate: one success plus the Gaussian stand-in for
+// b(N-1, p), clamped to [1, ceil N].
+__device__ __forceinline__ float open_count(uint32_t h1, float mu, float sig, float nceil, float* cc) {
+    *cc = 1.0f + mu + sig * normal_of_word(h1);
+    return fminf(fmaxf(floorf(*cc), 1.0f), nceil);
+}
+
+// --------------------------------------------------------------------------
 // material functions
 // --------------------------------------------------------------------------
 __device__ __forceinline__ float smith_lambda(int ndf, float ax, float ay, float wt, float wb, float wn) {
@@ -117,77 +151,80 @@ struct Vert {           // one tetrahedron vertex (a virtual grid)
 };
 
 // --------------------------------------------------------------------------
-// sinks: the image kernel ignores everything, the trace kernel records
+// Steps 1-5: everything about a pixel that does not depend on a light
 // --------------------------------------------------------------------------
-struct NoSink {
-    static constexpr bool kTrace = false;
-    __device__ void pix(int, int, float, float, float, float) {}
-    __device__ void rec(int, int, int, int, int, int, uint32_t, int, int, int, int, uint32_t, uint32_t,
-                        int, int, float, float, float, float, float, float, float, float) {}
+struct PixelSetup {
+    int status;         // 0 shaded, 1 background, 2 invalid
+    int K, Kmaj, ksub;
+    df A;               // flakes in the footprint
+    df ratio, phi;
+    df u, v;            // centre uv (exact float inputs)
+    df sig0, sig1, u0x, u0y;
+    Vert vert[4];
+    float ntr[4];       // trials of the 4 tetrahedron vertices (per sub-footprint)
+    df srho;
+    // shading frame and view direction (local frame), for the lights
+    df n[3], tg[3], b[3], wv[3];
+    float ax, ay, cos_v, lam_v;
 };
 
-struct LightState {
-    bool on;
-    float p, shade;
-    float v[4];
-    uint32_t A0[4], A1[4];
-    int32_t ax[4], ay[4];
-};
-
-template <int NLT, class Sink>
-__device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& sink) {
-    const int nL = NLT > 0 ? NLT : P.nL;
+__device__ __forceinline__ bool load_gbuf(const KParams& P, int px, float4& g0, float4& g1, float4& g2, float4& g3) {
     const float4* g = P.gbuf + (size_t)px * 4;
-    const float4 g0 = __ldg(g), g1 = __ldg(g + 1), g2 = __ldg(g + 2), g3 = __ldg(g + 3);
+    g0 = __ldg(g); g1 = __ldg(g + 1); g2 = __ldg(g + 2); g3 = __ldg(g + 3);
     const float gv[15] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z};
     bool finite = true;
 #pragma unroll
     for (int k = 0; k < 15; ++k) finite &= isfinite(gv[k]);
-    if (!finite) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+    return finite;
+}
+
+static __device__ __noinline__ void setup_pixel(const KParams& P, const Tables& T, int px, PixelSetup& S) {
+    S.status = 2;
+    S.K = 0;
+    float4 g0, g1, g2, g3;
+    if (!load_gbuf(P, px, g0, g1, g2, g3)) return;
 
     // ---- 1. shading frame (double-float: the angular texel coordinate
     //      h_t / gamma amplifies FP32 rounding of the frame ~20x) ----------
     const float nr[3] = {g1.z, g1.w, g2.x};
-    if (nr[0] == 0.0f && nr[1] == 0.0f && nr[2] == 0.0f) { sink.pix(1, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+    if (nr[0] == 0.0f && nr[1] == 0.0f && nr[2] == 0.0f) { S.status = 1; return; }
     const float tr[3] = {g2.y, g2.z, g2.w};
     const float vr[3] = {g3.x, g3.y, g3.z};
-    df n[3], tg[3], b[3];
     {
-        const df inl = 1.0f / dfsqrt(two_prod(nr[0], nr[0]) + two_prod(nr[1], nr[1]) + two_prod(nr[2], nr[2]));
-        n[0] = inl * nr[0]; n[1] = inl * nr[1]; n[2] = inl * nr[2];
+        const df inl = dfrsqrt(two_prod(nr[0], nr[0]) + two_prod(nr[1], nr[1]) + two_prod(nr[2], nr[2]));
+        S.n[0] = inl * nr[0]; S.n[1] = inl * nr[1]; S.n[2] = inl * nr[2];
     }
-    const df tn = n[0] * tr[0] + n[1] * tr[1] + n[2] * tr[2];
-    df tp[3] = {tr[0] - tn * n[0], tr[1] - tn * n[1], tr[2] - tn * n[2]};
+    const df tn = S.n[0] * tr[0] + S.n[1] * tr[1] + S.n[2] * tr[2];
+    df tp[3] = {tr[0] - tn * S.n[0], tr[1] - tn * S.n[1], tr[2] - tn * S.n[2]};
     const df tl2 = tp[0] * tp[0] + tp[1] * tp[1] + tp[2] * tp[2];
     const df vl2 = two_prod(vr[0], vr[0]) + two_prod(vr[1], vr[1]) + two_prod(vr[2], vr[2]);
-    if (!(tl2.hi > 0.0f) || !(vl2.hi > 0.0f)) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+    if (!(tl2.hi > 0.0f) || !(vl2.hi > 0.0f)) return;
     {
-        const df itl = 1.0f / dfsqrt(tl2);
-        tg[0] = tp[0] * itl; tg[1] = tp[1] * itl; tg[2] = tp[2] * itl;
+        const df itl = dfrsqrt(tl2);
+        S.tg[0] = tp[0] * itl; S.tg[1] = tp[1] * itl; S.tg[2] = tp[2] * itl;
     }
-    b[0] = n[1] * tg[2] - n[2] * tg[1];
-    b[1] = n[2] * tg[0] - n[0] * tg[2];
-    b[2] = n[0] * tg[1] - n[1] * tg[0];
-    // view direction in the local frame (t, b, n), unit length
-    df wv[3];
+    S.b[0] = S.n[1] * S.tg[2] - S.n[2] * S.tg[1];
+    S.b[1] = S.n[2] * S.tg[0] - S.n[0] * S.tg[2];
+    S.b[2] = S.n[0] * S.tg[1] - S.n[1] * S.tg[0];
     {
-        const df ivl = 1.0f / dfsqrt(vl2);
-        const df x = tg[0] * vr[0] + tg[1] * vr[1] + tg[2] * vr[2];
-        const df y = b[0] * vr[0] + b[1] * vr[1] + b[2] * vr[2];
-        const df z = n[0] * vr[0] + n[1] * vr[1] + n[2] * vr[2];
-        wv[0] = x * ivl; wv[1] = y * ivl; wv[2] = z * ivl;
+        const df ivl = dfrsqrt(vl2);
+        S.wv[0] = (S.tg[0] * vr[0] + S.tg[1] * vr[1] + S.tg[2] * vr[2]) * ivl;
+        S.wv[1] = (S.b[0] * vr[0] + S.b[1] * vr[1] + S.b[2] * vr[2]) * ivl;
+        S.wv[2] = (S.n[0] * vr[0] + S.n[1] * vr[1] + S.n[2] * vr[2]) * ivl;
     }
-    if (dfsign(wv[2]) <= 0) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
-    const float cos_v = wv[2].hi;
+    if (dfsign(S.wv[2]) <= 0) return;
+    S.cos_v = S.wv[2].hi;
 
-    float ax = P.ax, ay = P.ay;
-    df rho = ldf(P.rho), srho = ldf(P.sqrt_rho);
+    df rho = ldf(P.rho);
+    S.srho = ldf(P.sqrt_rho);
+    S.ax = P.ax; S.ay = P.ay;
     if (P.mat_px) {
         const float2 mp = __ldg(P.mat_px + px);
-        ax = ay = mp.x;
+        S.ax = S.ay = mp.x;
         rho = mkdf(mp.y);
-        srho = dfsqrt(rho);
+        S.srho = dfsqrt(rho);
     }
+    S.lam_v = smith_lambda(P.ndf, S.ax, S.ay, S.wv[0].hi, S.wv[1].hi, S.cos_v);
 
     // ---- 2. footprint (double-float) ----------------------------------
     // J = [[a, b], [c, d]] = [[du/dx, du/dy], [dv/dx, dv/dy]], pre-scaled by
@@ -204,46 +241,46 @@ __device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& si
     const df F = two_prod(ja, jc) + two_prod(jb, jd);
     const df det = dfabs(two_prod(ja, jd) - two_prod(jc, jb));
     const df Pft = scale2(det, 2 * je);                 // |det J| in uv^2
-    const df A = Pft * rho;                             // flakes in the footprint
-    if (!(A.hi > 0.0f)) { sink.pix(2, 0, 0.f, 0.f, 0.f, 0.f); return 0.0f; }
+    S.A = Pft * rho;                                    // flakes in the footprint
+    if (!(S.A.hi > 0.0f)) return;
     const df hm = scale2(E - G, -1);
     const df hyp = dfsqrt(hm * hm + F * F);
     const df s0sq = scale2(E + G, -1) + hyp;
     // ratio sigma0 / max(sigma1, 2^-20 sigma0): finite for line-like footprints
-    const df ratio = dflt(s0sq, scale2(det, 20)) ? s0sq / det : mkdf(1048576.0f);
-    df phi = scale2(dfatan2(scale2(F, 1), E - G, T.d), -1);
-    if (dfsign(phi) < 0) phi = phi + ldf(T.d.pi);
-    if (!dflt(phi, ldf(T.d.pi))) phi = phi - ldf(T.d.pi);
-    // major axis u0 of the footprint (eigenvector of J J^T for sigma0^2),
-    // oriented like (cos phi, sin phi) with phi in [0, pi)
-    df u0x, u0y;
-    {
-        df ex, ey;
-        if (dfsign(hm) >= 0) { ex = hyp + hm; ey = F; } else { ex = F; ey = hyp - hm; }
-        if (ex.hi == 0.0f && ey.hi == 0.0f) ex = mkdf(1.0f);
-        const df inv = 1.0f / dfsqrt(ex * ex + ey * ey);
-        u0x = ex * inv; u0y = ey * inv;
-        if (dfsign(u0y) < 0 || (dfsign(u0y) == 0 && dfsign(u0x) < 0)) { u0x = -u0x; u0y = -u0y; }
-    }
-    const df sig0 = scale2(dfsqrt(s0sq), je);
-    const df sig1 = Pft / sig0;
+    S.ratio = dflt(s0sq, scale2(det, 20)) ? s0sq / det : mkdf(1048576.0f);
+    S.phi = scale2(dfatan2(scale2(F, 1), E - G, T.d), -1);
+    if (dfsign(S.phi) < 0) S.phi = S.phi + ldf(T.d.pi);
+    if (!dflt(S.phi, ldf(T.d.pi))) S.phi = S.phi - ldf(T.d.pi);
+    S.u = mkdf(g0.x); S.v = mkdf(g0.y);
 
     // ---- 3. sub-footprints --------------------------------------------
     int Kmaj = 1;
-    const df rq = scale2(ratio, -P.M);
+    const df rq = scale2(S.ratio, -P.M);
     if (dfsign(rq - 1.0f) > 0) {
         df fr;
         int c = dffloor(rq, &fr);           // rq <= 2^19 (ratio capped at 2^20)
         if (dfsign(fr) > 0) c += 1;
         Kmaj = c >= P.Kmax ? P.Kmax : c;
     }
-    const df Ap = A / (float)Kmaj;
+    const df Ap = A_over(S.A, Kmaj);
     int ksub = 1;
     while (dflt(mkdf((float)(ksub * ksub) * P.top), Ap) && Kmaj * (ksub + 1) * (ksub + 1) <= P.Kmax) ++ksub;
     const int K = Kmaj * ksub * ksub;
-    const df As = A / (float)K;
-    const df rho_r = dflog2(ratio, T.d) - dflog2(mkdf((float)Kmaj), T.d);
-    sink.pix(0, K, A.hi, ratio.hi, phi.hi, 0.0f);
+    S.Kmaj = Kmaj; S.ksub = ksub; S.K = K;
+    const df As = A_over(S.A, K);
+    const df rho_r = dflog2(S.ratio, T.d) - dflog2(mkdf((float)Kmaj), T.d);
+    if (K > 1) {
+        // major axis u0 of the footprint (eigenvector of J J^T for sigma0^2),
+        // oriented like (cos phi, sin phi) with phi in [0, pi)
+        df ex, ey;
+        if (dfsign(hm) >= 0) { ex = hyp + hm; ey = F; } else { ex = F; ey = hyp - hm; }
+        if (ex.hi == 0.0f && ey.hi == 0.0f) ex = mkdf(1.0f);
+        const df inv = dfrsqrt(ex * ex + ey * ey);
+        S.u0x = ex * inv; S.u0y = ey * inv;
+        if (dfsign(S.u0y) < 0 || (dfsign(S.u0y) == 0 && dfsign(S.u0x) < 0)) { S.u0x = -S.u0x; S.u0y = -S.u0y; }
+        S.sig0 = scale2(dfsqrt(s0sq), je);
+        S.sig1 = Pft / S.sig0;
+    }
 
     // ---- 4. LOD bracket -------------------------------------------------
     int level;
@@ -270,7 +307,7 @@ __device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& si
     const df x = rr - (float)m;
     const int nm = m == 0 ? 4 : (1 << (m + 1));
     df t;
-    int a = dffloor(scale2(phi * ldf(T.d.inv_pi), m == 0 ? 2 : m + 1), &t);
+    int a = dffloor(scale2(S.phi * ldf(T.d.inv_pi), m == 0 ? 2 : m + 1), &t);
     a %= nm;
     Vert tv[3];
     df lam[3];
@@ -296,212 +333,161 @@ __device__ float shade_pixel(const KParams& P, const Tables& T, int px, Sink& si
         }
     }
     // prism split by vertex order: upper weight of vertex j = clamp(s - C_j, 0, lam_j)
-    int vtri[4], vup[4], tet;
+    int vtri[4], vup[4];
     df w[4];
     const df C1 = lam[0], C2 = lam[0] + lam[1];
     if (dfle(s, C1)) {
-        tet = 1;
         vtri[0] = 0; vup[0] = 0; w[0] = lam[0] - s;
         vtri[1] = 1; vup[1] = 0; w[1] = lam[1];
         vtri[2] = 2; vup[2] = 0; w[2] = lam[2];
         vtri[3] = 0; vup[3] = 1; w[3] = s;
     } else if (dfle(s, C2)) {
-        tet = 2;
         vtri[0] = 1; vup[0] = 0; w[0] = lam[1] - (s - C1);
         vtri[1] = 2; vup[1] = 0; w[1] = lam[2];
         vtri[2] = 0; vup[2] = 1; w[2] = lam[0];
         vtri[3] = 1; vup[3] = 1; w[3] = s - C1;
     } else {
-        tet = 3;
         vtri[0] = 2; vup[0] = 0; w[0] = lam[2] - (s - C2);
         vtri[1] = 0; vup[1] = 1; w[1] = lam[0];
         vtri[2] = 1; vup[2] = 1; w[2] = lam[1];
         vtri[3] = 2; vup[3] = 1; w[3] = s - C2;
     }
-    Vert vert[4];
-    float ntr[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        vert[i] = tv[vtri[i]];
-        vert[i].level = level + vup[i];
-        const df ni = pinned ? w[i] * As : scale2(w[i], vert[i].level * P.log2f);
-        ntr[i] = ni.hi;
+        S.vert[i] = tv[vtri[i]];
+        S.vert[i].level = level + vup[i];
+        const df ni = pinned ? w[i] * As : scale2(w[i], S.vert[i].level * P.log2f);
+        S.ntr[i] = ni.hi;
     }
-    (void)tet;
+    S.status = 0;
+}
 
-    // ---- 7a. per-light state (independent of the sub-footprint) ---------
-    constexpr int NLA = NLT > 0 ? NLT : kMaxLights;
-    LightState ls[NLA];
-    const float Dn = 1.0f / (3.14159265358979f * ax * ay);
-    const float lam_v = smith_lambda(P.ndf, ax, ay, wv[0].hi, wv[1].hi, cos_v);
+// --------------------------------------------------------------------------
+// Step 7a: per light (independent of the sub-footprint)
+// --------------------------------------------------------------------------
+struct LightState {
+    bool on;
+    float p, shade;               // p of Eq. 4; F G D(n) E / (4 R cos_v)
+    float v[4];                   // angular bilinear weights
+    uint32_t A0[4], A1[4];        // angular hash words
+    int32_t ax[4], ay[4];         // angular texels (traces)
+};
+
+static __device__ __noinline__ void setup_light(const KParams& P, const PixelSetup& S, int px, int l, LightState& L) {
+    L.on = false;
+    const KLight kl = P.lights[l];
+    float lr[3], E;
+    if (kl.kind == 0) {
+        const float4 lp = __ldg(P.light_px + (size_t)l * P.npx + px);
+        lr[0] = lp.x; lr[1] = lp.y; lr[2] = lp.z; E = lp.w;
+    } else {
+        lr[0] = kl.dx; lr[1] = kl.dy; lr[2] = kl.dz; E = kl.E;
+    }
+    const df ll2 = two_prod(lr[0], lr[0]) + two_prod(lr[1], lr[1]) + two_prod(lr[2], lr[2]);
+    if (!(ll2.hi > 0.0f)) return;
+    // light direction in the local frame, unit length
+    df wl[3];
+    {
+        const df il = dfrsqrt(ll2);
+        wl[0] = (S.tg[0] * lr[0] + S.tg[1] * lr[1] + S.tg[2] * lr[2]) * il;
+        wl[1] = (S.b[0] * lr[0] + S.b[1] * lr[1] + S.b[2] * lr[2]) * il;
+        wl[2] = (S.n[0] * lr[0] + S.n[1] * lr[1] + S.n[2] * lr[2]) * il;
+    }
+    if (dfsign(wl[2]) <= 0) return;
+    const float cos_l = wl[2].hi;
+    df h[3] = {S.wv[0] + wl[0], S.wv[1] + wl[1], S.wv[2] + wl[2]};
+    {
+        const df ih = dfrsqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+        h[0] = h[0] * ih; h[1] = h[1] * ih; h[2] = h[2] * ih;
+    }
+    const float ht = h[0].hi, hb = h[1].hi, hn = h[2].hi;
+    // Eq. 4: p = R D(h) / D(n)
+    const float e = (ht / S.ax) * (ht / S.ax) + (hb / S.ay) * (hb / S.ay);
+    const float hn2 = hn * hn;
+    const float rat = P.ndf == 0 ? expf(-e / hn2) / (hn2 * hn2) : 1.0f / ((e + hn2) * (e + hn2));
+    L.p = fminf(P.R * rat, 1.0f);
+    // Eq. 14: bilinear angular texels of the projected half-vector; the
+    // weights are formed from double-float fractions so each keeps full
+    // relative precision however small it is.
+    df fxd, fyd;
+    const float ig = 1.0f / P.gamma;
+    const int ix = dffloor(div_by(h[0], P.gamma, ig), &fxd);
+    const int iy = dffloor(div_by(h[1], P.gamma, ig), &fyd);
+    const float fx = fxd.hi, fy = fyd.hi;
+    const float gx = (1.0f - fxd).hi, gy = (1.0f - fyd).hi;
+    L.v[0] = gx * gy; L.v[1] = fx * gy;
+    L.v[2] = gx * fy; L.v[3] = fx * fy;
 #pragma unroll
-    for (int l = 0; l < NLA; ++l) {
-        LightState& L = ls[l];
-        L.on = false;
-        if (l >= nL) continue;
-        const KLight kl = P.lights[l];
-        float lr[3], E;
-        if (kl.kind == 0) {
-            const float4 lp = __ldg(P.light_px + (size_t)l * P.npx + px);
-            lr[0] = lp.x; lr[1] = lp.y; lr[2] = lp.z; E = lp.w;
-        } else {
-            lr[0] = kl.dx; lr[1] = kl.dy; lr[2] = kl.dz; E = kl.E;
-        }
-        const df ll2 = two_prod(lr[0], lr[0]) + two_prod(lr[1], lr[1]) + two_prod(lr[2], lr[2]);
-        if (!(ll2.hi > 0.0f)) continue;
-        // light direction in the local frame, unit length
-        df wl[3];
-        {
-            const df il = 1.0f / dfsqrt(ll2);
-            wl[0] = (tg[0] * lr[0] + tg[1] * lr[1] + tg[2] * lr[2]) * il;
-            wl[1] = (b[0] * lr[0] + b[1] * lr[1] + b[2] * lr[2]) * il;
-            wl[2] = (n[0] * lr[0] + n[1] * lr[1] + n[2] * lr[2]) * il;
-        }
-        if (dfsign(wl[2]) <= 0) continue;
-        const float cos_l = wl[2].hi;
-        df h[3] = {wv[0] + wl[0], wv[1] + wl[1], wv[2] + wl[2]};
-        {
-            const df ih = 1.0f / dfsqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
-            h[0] = h[0] * ih; h[1] = h[1] * ih; h[2] = h[2] * ih;
-        }
-        const float ht = h[0].hi, hb = h[1].hi, hn = h[2].hi;
-        // Eq. 4: p = R D(h) / D(n)
-        const float e = (ht / ax) * (ht / ax) + (hb / ay) * (hb / ay);
-        const float hn2 = hn * hn;
-        const float rat = P.ndf == 0 ? expf(-e / hn2) / (hn2 * hn2) : 1.0f / ((e + hn2) * (e + hn2));
-        L.p = fminf(P.R * rat, 1.0f);
-        // Eq. 14: bilinear angular texels of the projected half-vector; the
-        // weights are formed from double-float fractions so each keeps full
-        // relative precision however small it is.
+    for (int k = 0; k < 4; ++k) {
+        L.ax[k] = ix + (k & 1); L.ay[k] = iy + (k >> 1);
+        uint32_t hx = (uint32_t)L.ax[k], hy = (uint32_t)L.ay[k], hz = ~P.seed;
+        pcg3d(hx, hy, hz);
+        L.A0[k] = hx; L.A1[k] = hy;
+    }
+    // Eq. 2 with D_P = D(n)/R C/A: out_l = F G D(n) E / (4 R cos_v) * C / A
+    const float vh = S.wv[0].hi * ht + S.wv[1].hi * hb + S.cos_v * hn;
+    const float om = 1.0f - vh;
+    const float Fr = P.F0 + (1.0f - P.F0) * (om * om) * (om * om) * om;
+    const float lam_l = smith_lambda(P.ndf, S.ax, S.ay, wl[0].hi, wl[1].hi, cos_l);
+    const float Gs = 1.0f / ((1.0f + S.lam_v) * (1.0f + lam_l));
+    const float Dn = 1.0f / (3.14159265358979f * S.ax * S.ay);
+    L.shade = Fr * Gs * Dn * E / (4.0f * P.R * S.cos_v);
+    L.on = true;
+}
+
+// --------------------------------------------------------------------------
+// Step 6: spatial texels of one sub-footprint (12 = 4 grids x 3 simplex vertices)
+// --------------------------------------------------------------------------
+struct SubState {
+    uint32_t S0[12], S1[12];      // spatial hash words
+    float uw[12];                 // barycentric weights
+    int32_t li[12], lj[12];       // lattice vertices (traces)
+    uint32_t gid[4];
+};
+
+// returns false when a lattice coordinate leaves |q| < 2^30
+static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T, const PixelSetup& S, int sub, SubState& U) {
+    df us = S.u, vs = S.v;
+    if (S.K > 1) {
+        // centre of sub-rectangle (ia, ib) of the sigma0 x sigma1 rectangle
+        // aligned with (u0, u1 = (-u0y, u0x))
+        const int ncols = S.Kmaj * S.ksub;
+        const int ia = sub % ncols, ib = sub / ncols;
+        const df oa = S.sig0 * div_by(mkdf((float)(2 * ia + 1 - ncols)), (float)(2 * ncols), 1.0f / (float)(2 * ncols));
+        const df ob = S.sig1 * div_by(mkdf((float)(2 * ib + 1 - S.ksub)), (float)(2 * S.ksub), 1.0f / (float)(2 * S.ksub));
+        us = us + (oa * S.u0x - ob * S.u0y);
+        vs = vs + (oa * S.u0y + ob * S.u0x);
+    }
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+        const Vert V = S.vert[i];
+        U.gid[i] = ((uint32_t)V.level << 16) | ((uint32_t)V.ring << 8) | (uint32_t)V.kor;
+        const RotEntry Q = T.rot[rot_index(V.ring, V.kor)];
+        df sl;
+        if (P.f == 4) sl = scale2(S.srho, -V.level);
+        else sl = (V.level & 1) ? scale2(S.srho * ldf(T.d.inv_sqrt2), -(V.level >> 1)) : scale2(S.srho, -(V.level >> 1));
+        const df qx = sl * (df{Q.r0.x, Q.r0.y} * us + df{Q.r0.z, Q.r0.w} * vs);
+        const df qy = sl * (df{Q.r1.x, Q.r1.y} * us + df{Q.r1.z, Q.r1.w} * vs);
+        if (!(fabsf(qx.hi) < 1073741824.0f) || !(fabsf(qy.hi) < 1073741824.0f)) return false;
         df fxd, fyd;
-        const int ix = dffloor(h[0] / P.gamma, &fxd);
-        const int iy = dffloor(h[1] / P.gamma, &fyd);
-        const float fx = fxd.hi, fy = fyd.hi;
-        const float gx = (1.0f - fxd).hi, gy = (1.0f - fyd).hi;
-        L.v[0] = gx * gy; L.v[1] = fx * gy;
-        L.v[2] = gx * fy; L.v[3] = fx * fy;
+        const int i0 = dffloor(qx, &fxd);
+        const int j0 = dffloor(qy, &fyd);
+        // barycentric weights from double-float fractions (full relative precision)
+        const bool lower = !dflt(fxd, fyd);
+        U.li[3 * i + 0] = i0; U.lj[3 * i + 0] = j0;
+        U.uw[3 * i + 0] = (1.0f - (lower ? fxd : fyd)).hi;
+        U.li[3 * i + 1] = lower ? i0 + 1 : i0; U.lj[3 * i + 1] = lower ? j0 : j0 + 1;
+        U.uw[3 * i + 1] = (lower ? fxd - fyd : fyd - fxd).hi;
+        U.li[3 * i + 2] = i0 + 1; U.lj[3 * i + 2] = j0 + 1;
+        U.uw[3 * i + 2] = (lower ? fyd : fxd).hi;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            L.ax[k] = ix + (k & 1); L.ay[k] = iy + (k >> 1);
-            uint32_t hx = (uint32_t)L.ax[k], hy = (uint32_t)L.ay[k], hz = ~P.seed;
-            pcg3d(hx, hy, hz);
-            L.A0[k] = hx; L.A1[k] = hy;
-        }
-        // Eq. 2 with D_P = D(n)/R C/A: out_l = F G D(n) E / (4 R cos_v) * C / A
-        const float vh = wv[0].hi * ht + wv[1].hi * hb + cos_v * hn;
-        const float om = 1.0f - vh;
-        const float Fr = P.F0 + (1.0f - P.F0) * (om * om) * (om * om) * om;
-        const float lam_l = smith_lambda(P.ndf, ax, ay, wl[0].hi, wl[1].hi, cos_l);
-        const float Gs = 1.0f / ((1.0f + lam_v) * (1.0f + lam_l));
-        L.shade = Fr * Gs * Dn * E / (4.0f * P.R * cos_v);
-        L.on = true;
-    }
-
-    // ---- 6/7b. sub-footprints x lights x 48 evaluations ----------------
-    float C[NLA];
-#pragma unroll
-    for (int l = 0; l < NLA; ++l) C[l] = 0.0f;
-    const int ncols = Kmaj * ksub;
-    int status = 0;
-    for (int sub = 0; sub < K && status == 0; ++sub) {
-        df us = mkdf(g0.x), vs = mkdf(g0.y);
-        if (K > 1) {
-            // centre of sub-rectangle (ia, ib) of the sigma0 x sigma1 rectangle
-            // aligned with (u0, u1 = (-u0y, u0x))
-            const int ia = sub % ncols, ib = sub / ncols;
-            const df oa = sig0 * (mkdf((float)(2 * ia + 1 - ncols)) / (float)(2 * ncols));
-            const df ob = sig1 * (mkdf((float)(2 * ib + 1 - ksub)) / (float)(2 * ksub));
-            us = us + (oa * u0x - ob * u0y);
-            vs = vs + (oa * u0y + ob * u0x);
-        }
-        uint32_t S0[4][3], S1[4][3];
-        float uw[4][3];
-        int32_t li[4][3], lj[4][3];
-        uint32_t gid[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const Vert V = vert[i];
-            gid[i] = ((uint32_t)V.level << 16) | ((uint32_t)V.ring << 8) | (uint32_t)V.kor;
-            const RotEntry Q = T.rot[rot_index(V.ring, V.kor)];
-            df sl;
-            if (P.f == 4) sl = scale2(srho, -V.level);
-            else sl = (V.level & 1) ? scale2(srho * ldf(T.d.inv_sqrt2), -(V.level >> 1)) : scale2(srho, -(V.level >> 1));
-            const df qx = sl * (df{Q.r0.x, Q.r0.y} * us + df{Q.r0.z, Q.r0.w} * vs);
-            const df qy = sl * (df{Q.r1.x, Q.r1.y} * us + df{Q.r1.z, Q.r1.w} * vs);
-            if (!(fabsf(qx.hi) < 1073741824.0f) || !(fabsf(qy.hi) < 1073741824.0f)) { status = 3; break; }
-            df fxd, fyd;
-            const int i0 = dffloor(qx, &fxd);
-            const int j0 = dffloor(qy, &fyd);
-            // barycentric weights from double-float fractions (full relative precision)
-            if (!dflt(fxd, fyd)) {
-                li[i][0] = i0;     lj[i][0] = j0;     uw[i][0] = (1.0f - fxd).hi;
-                li[i][1] = i0 + 1; lj[i][1] = j0;     uw[i][1] = (fxd - fyd).hi;
-                li[i][2] = i0 + 1; lj[i][2] = j0 + 1; uw[i][2] = fyd.hi;
-            } else {
-                li[i][0] = i0;     lj[i][0] = j0;     uw[i][0] = (1.0f - fyd).hi;
-                li[i][1] = i0;     lj[i][1] = j0 + 1; uw[i][1] = (fyd - fxd).hi;
-                li[i][2] = i0 + 1; lj[i][2] = j0 + 1; uw[i][2] = fxd.hi;
-            }
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                uint32_t hx = (uint32_t)li[i][j], hy = (uint32_t)lj[i][j], hz = gid[i], hw = P.seed;
-                pcg4d(hx, hy, hz, hw);
-                S0[i][j] = hx; S1[i][j] = hy;
-            }
-        }
-        if (status) break;
-#pragma unroll
-        for (int l = 0; l < NLA; ++l) {
-            if (!ls[l].on) continue;
-            const LightState& L = ls[l];
-            float acc = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                // Sec. 6.3: gated Gaussian binomial with N = n_i trials
-                const float nn = ntr[i];
-                float P1 = 0.0f;
-                if (nn > 0.0f && L.p > 0.0f) P1 = L.p >= 1.0f ? 1.0f : -expm1f(nn * log1pf(-L.p));
-                const uint32_t Tg = (uint32_t)ceilf(P1 * 33554432.0f);      // 2^25
-                const float nm1 = nn > 1.0f ? nn - 1.0f : 0.0f;
-                const float mu = nm1 * L.p;
-                const float var = mu * (1.0f - L.p);
-                const float sig = var > 0.0f ? sqrtf(var) : 0.0f;
-                const float nceil = ceilf(nn);
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint32_t h0 = fmix32(S0[i][j] + L.A0[k]);
-                        // theta0 < P1  <=>  2 (h0 >> 8) + 1 < P1 2^25
-                        const bool gate = ((h0 >> 7) | 1u) < Tg;
-                        float c = 0.0f;
-                        float cc = 0.0f;
-                        uint32_t h1 = 0;
-                        if (gate || Sink::kTrace) h1 = fmix32(S1[i][j] + L.A1[k]);
-                        if (gate) {
-                            cc = 1.0f + mu + sig * normal_of_word(h1);
-                            c = fminf(fmaxf(floorf(cc), 1.0f), nceil);
-                            acc += uw[i][j] * L.v[k] * c;
-                        }
-                        if (Sink::kTrace)
-                            sink.rec((((l * K + sub) * 4 + i) * 3 + j) * 4 + k, l, sub, i, j, k, gid[i],
-                                     li[i][j], lj[i][j], L.ax[k], L.ay[k], h0, h1, gate ? 1 : 0,
-                                     c < 2147483647.0f ? (int)c : 2147483647,
-                                     nn, P1, mu, sig, cc, uw[i][j], L.v[k], L.p);
-                    }
-                }
-            }
-            C[l] += acc;
+        for (int j = 0; j < 3; ++j) {
+            uint32_t hx = (uint32_t)U.li[3 * i + j], hy = (uint32_t)U.lj[3 * i + j], hz = U.gid[i], hw = P.seed;
+            pcg4d(hx, hy, hz, hw);
+            U.S0[3 * i + j] = hx; U.S1[3 * i + j] = hy;
         }
     }
-    if (status) { sink.pix(status, K, A.hi, ratio.hi, phi.hi, 0.0f); return 0.0f; }
-    float out = 0.0f;
-#pragma unroll
-    for (int l = 0; l < NLA; ++l)
-        if (ls[l].on) out += ls[l].shade * C[l];
-    out = out / A.hi;
-    sink.pix(0, K, A.hi, ratio.hi, phi.hi, out);
-    return out;
+    return true;
 }
 
 }  // namespace glint
