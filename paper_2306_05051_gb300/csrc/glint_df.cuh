@@ -45,11 +45,13 @@ __device__ __forceinline__ df two_prod(float a, float b) {
 
 __device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
 
+// Sum with absolute error ~2^-48 (|a| + |b|) (Dekker's composition): the
+// chains here need accuracy relative to the operands, not to a cancelled
+// result; the interpolation weights, which do need relative accuracy, are
+// formed from exact residuals (see dffloor_w).
 __device__ __forceinline__ df operator+(df a, df b) {
     const df s = two_sum(a.hi, b.hi);
-    const df t = two_sum(a.lo, b.lo);
-    const df v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-    return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+    return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, a.lo), b.lo));
 }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
 
@@ -127,10 +129,11 @@ __device__ __forceinline__ int dfsign(df a) {
     if (a.hi < 0.0f) return -1;
     return a.lo > 0.0f ? 1 : (a.lo < 0.0f ? -1 : 0);
 }
-__device__ __forceinline__ bool dfle(df a, df b) { return dfsign(a - b) <= 0; }
-__device__ __forceinline__ bool dflt(df a, df b) { return dfsign(a - b) < 0; }
-__device__ __forceinline__ bool dfle(df a, float b) { return dfsign(a - b) <= 0; }
-__device__ __forceinline__ bool dflt(df a, float b) { return dfsign(a - b) < 0; }
+// Order of normalised double-floats (hi = fl(hi + lo)) is lexicographic.
+__device__ __forceinline__ bool dflt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool dfle(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+__device__ __forceinline__ bool dflt(df a, float b) { return a.hi < b || (a.hi == b && a.lo < 0.0f); }
+__device__ __forceinline__ bool dfle(df a, float b) { return a.hi < b || (a.hi == b && a.lo <= 0.0f); }
 __device__ __forceinline__ df dfabs(df a) { return dfsign(a) < 0 ? -a : a; }
 
 // floor: integer part and fraction in [0, 1); requires |a| < 2^31.  The
@@ -138,13 +141,27 @@ __device__ __forceinline__ df dfabs(df a) { return dfsign(a) < 0 ? -a : a; }
 __device__ __forceinline__ int dffloor(df a, df* frac) {
     const float f = floorf(a.hi);
     df r = fast_two_sum(__fsub_rn(a.hi, f), a.lo);   // a.hi - f is exact
-    // above 2^24 the low word alone can exceed 1 in magnitude
-    const float g = floorf(r.hi);
-    r = r - g;
-    int i = (int)f + (int)g;
-    if (dfsign(r) < 0) { i -= 1; r = r + 1.0f; }
+    int i = (int)f;
+    if (fabsf(a.hi) >= 16777216.0f) {
+        // above 2^24 the low word alone can exceed 1 in magnitude
+        const float g = floorf(r.hi);
+        r = r - g;
+        i += (int)g;
+    }
+    if (r.hi < 0.0f || (r.hi == 0.0f && r.lo < 0.0f)) { i -= 1; r = r + 1.0f; }
     else if (!dflt(r, 1.0f)) { i += 1; r = r - 1.0f; }
     *frac = r;
+    return i;
+}
+
+// Floor with the two interpolation weights of the cell: f = a - floor(a)
+// and g = 1 - f, each rounded once to FP32 (full relative precision even
+// when tiny: 1 - r.hi is exact whenever r.hi >= 1/2).
+__device__ __forceinline__ int dffloor_w(df a, float* f, float* g) {
+    df r;
+    const int i = dffloor(a, &r);
+    *f = __fadd_rn(r.hi, r.lo);
+    *g = __fsub_rn(__fsub_rn(1.0f, r.hi), r.lo);
     return i;
 }
 

@@ -147,11 +147,14 @@ __global__ void __launch_bounds__(256) fwd_kernel(const __grid_constant__ KParam
     __shared__ Tables T;
     __shared__ WarpQueue Qs[kWarpsPerBlock];
     load_tables(P, T);
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
     WarpQueue& q = Qs[wib];
-    const int nw = gridDim.x * kWarpsPerBlock;
-    for (int base = (blockIdx.x * kWarpsPerBlock + wib) * 32; base < P.npx; base += nw * 32) {
-        const int px = base + lane;
+    // Block-uniform tiles of 256 pixels.  The barrier at the top of a tile
+    // keeps the block's warps close together in the (long, mostly
+    // straight-line) setup code so they share instruction-cache lines.
+    for (int base = blockIdx.x * blockDim.x; base < P.npx; base += gridDim.x * blockDim.x) {
+        __syncthreads();
+        const int px = base + (int)threadIdx.x;
         const float o = shade_warp(P, T, q, px, px < P.npx);
         if (px < P.npx) P.out[px] = o;
     }

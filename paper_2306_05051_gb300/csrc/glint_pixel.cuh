@@ -409,12 +409,10 @@ static __device__ __noinline__ void setup_light(const KParams& P, const PixelSet
     // Eq. 14: bilinear angular texels of the projected half-vector; the
     // weights are formed from double-float fractions so each keeps full
     // relative precision however small it is.
-    df fxd, fyd;
-    const float ig = 1.0f / P.gamma;
-    const int ix = dffloor(div_by(h[0], P.gamma, ig), &fxd);
-    const int iy = dffloor(div_by(h[1], P.gamma, ig), &fyd);
-    const float fx = fxd.hi, fy = fyd.hi;
-    const float gx = (1.0f - fxd).hi, gy = (1.0f - fyd).hi;
+    float fx, gx, fy, gy;
+    const float ig = approx_rcp(P.gamma);
+    const int ix = dffloor_w(div_by(h[0], P.gamma, ig), &fx, &gx);
+    const int iy = dffloor_w(div_by(h[1], P.gamma, ig), &fy, &gy);
     L.v[0] = gx * gy; L.v[1] = fx * gy;
     L.v[2] = gx * fy; L.v[3] = fx * fy;
 #pragma unroll
@@ -472,14 +470,17 @@ static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T,
         df fxd, fyd;
         const int i0 = dffloor(qx, &fxd);
         const int j0 = dffloor(qy, &fyd);
-        // barycentric weights from double-float fractions (full relative precision)
+        // barycentric weights, each rounded once from double-float fractions
+        // (full relative precision)
         const bool lower = !dflt(fxd, fyd);
+        const df hi = lower ? fxd : fyd, lo = lower ? fyd : fxd;     // larger / smaller fraction
+        const df dd = hi - lo;
         U.li[3 * i + 0] = i0; U.lj[3 * i + 0] = j0;
-        U.uw[3 * i + 0] = (1.0f - (lower ? fxd : fyd)).hi;
+        U.uw[3 * i + 0] = __fsub_rn(__fsub_rn(1.0f, hi.hi), hi.lo);
         U.li[3 * i + 1] = lower ? i0 + 1 : i0; U.lj[3 * i + 1] = lower ? j0 : j0 + 1;
-        U.uw[3 * i + 1] = (lower ? fxd - fyd : fyd - fxd).hi;
+        U.uw[3 * i + 1] = __fadd_rn(dd.hi, dd.lo);
         U.li[3 * i + 2] = i0 + 1; U.lj[3 * i + 2] = j0 + 1;
-        U.uw[3 * i + 2] = (lower ? fyd : fxd).hi;
+        U.uw[3 * i + 2] = __fadd_rn(lo.hi, lo.lo);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             uint32_t hx = (uint32_t)U.li[3 * i + j], hy = (uint32_t)U.lj[3 * i + j], hz = U.gid[i], hw = P.seed;
