@@ -124,6 +124,20 @@ int glint_version(void);
 int glint_eval(const GlintFrame* frame, const GlintMaterial* material,
                const GlintLight* lights, float* out, void* stream);
 
+/* Launch shape of the forward kernel: threads per CTA (128, 256, 512 or
+ * 1024; one warp shades 32 consecutive pixels, a CTA a tile of that many
+ * pixels) and resident CTAs per SM the grid is sized for (1..16).  The grid
+ * is persistent: min(tiles, SMs x ctas_per_sm) CTAs loop over the tiles. */
+typedef struct GlintLaunch {
+    int32_t threads_per_cta;
+    int32_t ctas_per_sm;
+} GlintLaunch;
+
+/* glint_eval with an explicit launch shape (used by the autotuner).  Same
+ * result bits as glint_eval for every shape. */
+int glint_eval_launch(const GlintFrame* frame, const GlintMaterial* material,
+                      const GlintLight* lights, float* out, const GlintLaunch* launch, void* stream);
+
 /* The same evaluation with host buffers: copies every plane of `frame`
  * (host pointers, ideally pinned) into `staging` (device, caller-owned, at
  * least glint_eval_host_staging_size() bytes), evaluates, and copies the

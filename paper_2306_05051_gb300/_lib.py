@@ -35,6 +35,10 @@ class GlintLight(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dir", C.c_float * 3), ("intensity", C.c_float)]
 
 
+class GlintLaunch(C.Structure):
+    _fields_ = [("threads_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
 class GlintFrame(C.Structure):
     _fields_ = [("gbuf", C.c_void_p), ("light_px", C.c_void_p), ("mat_px", C.c_void_p),
                 ("width", C.c_int32), ("height", C.c_int32), ("n_lights", C.c_int32)]
@@ -54,6 +58,7 @@ SIGNATURES = {
     "glint_error_string": (C.c_char_p, [C.c_int]),
     "glint_version": (C.c_int, []),
     "glint_eval": (C.c_int, [_P, _P, _P, _P, _P]),
+    "glint_eval_launch": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "glint_eval_host_staging_size": (C.c_size_t, [C.c_int32] * 5),
     "glint_eval_host": (C.c_int, [_P, _P, _P, _P, _P, C.c_size_t, _P]),
     "glint_eval_trace": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, C.c_int32, _P]),

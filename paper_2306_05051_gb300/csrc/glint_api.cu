@@ -100,6 +100,8 @@ int check_device_ptr(const void* p, size_t align) {
 
 std::mutex g_dev_mutex;
 int g_sm_count[64];
+constexpr int kDefaultThreads = 512;
+constexpr int kDefaultCtasPerSm = 2;
 
 }  // namespace
 
@@ -157,13 +159,14 @@ int check_frame_device(const GlintFrame* f, const GlintLight* lights) {
     return GLINT_OK;
 }
 
-FwdLaunch default_fwd_launch(int npx) {
-    const int threads = 256;
+FwdLaunch make_fwd_launch(int npx, int threads, int ctas_per_sm) {
     const int sms = num_sms() > 0 ? num_sms() : 1;
     const int need = (npx + threads - 1) / threads;
-    const int cap = sms * 8;
+    const int cap = sms * ctas_per_sm;
     return FwdLaunch{threads, need < cap ? need : cap};
 }
+
+FwdLaunch default_fwd_launch(int npx) { return make_fwd_launch(npx, kDefaultThreads, kDefaultCtasPerSm); }
 
 int cuda_rc(cudaError_t e) {
     if (e == cudaSuccess) return GLINT_OK;
@@ -191,6 +194,20 @@ const char* glint_error_string(int code) {
 }
 
 int glint_version(void) { return 100; }
+
+int glint_eval_launch(const GlintFrame* frame, const GlintMaterial* material, const GlintLight* lights,
+                      float* out, const GlintLaunch* launch, void* stream) {
+    if (!launch) return GLINT_ERR_ARG;
+    const int t = launch->threads_per_cta;
+    if ((t != 128 && t != 256 && t != 512 && t != 1024) || launch->ctas_per_sm < 1 || launch->ctas_per_sm > 16)
+        return GLINT_ERR_ARG;
+    KParams P;
+    int rc = make_params(frame, material, lights, out, &P);
+    if (rc) return rc;
+    if ((rc = check_frame_device(frame, lights))) return rc;
+    if ((rc = check_device_ptr(out, 4))) return rc;
+    return cuda_rc(launch_fwd(P, (cudaStream_t)stream, make_fwd_launch(P.npx, t, launch->ctas_per_sm)));
+}
 
 int glint_eval(const GlintFrame* frame, const GlintMaterial* material, const GlintLight* lights, float* out,
                void* stream) {

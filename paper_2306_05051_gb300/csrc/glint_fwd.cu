@@ -143,14 +143,14 @@ __device__ float shade_warp(const KParams& P, const Tables& T, WarpQueue& q, int
     return acc / S.A.hi;
 }
 
-__global__ void __launch_bounds__(256) fwd_kernel(const __grid_constant__ KParams P) {
-    __shared__ Tables T;
-    __shared__ WarpQueue Qs[kWarpsPerBlock];
+__global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Tables& T = *reinterpret_cast<Tables*>(smem);
+    WarpQueue* Qs = reinterpret_cast<WarpQueue*>(smem + sizeof(Tables));
     load_tables(P, T);
-    const int wib = threadIdx.x >> 5;
-    WarpQueue& q = Qs[wib];
-    // Block-uniform tiles of 256 pixels.  The barrier at the top of a tile
-    // keeps the block's warps close together in the (long, mostly
+    WarpQueue& q = Qs[threadIdx.x >> 5];
+    // Block-uniform tiles of blockDim.x pixels.  The barrier at the top of a
+    // tile keeps the block's warps together in the (long, mostly
     // straight-line) setup code so they share instruction-cache lines.
     for (int base = blockIdx.x * blockDim.x; base < P.npx; base += gridDim.x * blockDim.x) {
         __syncthreads();
@@ -159,6 +159,8 @@ __global__ void __launch_bounds__(256) fwd_kernel(const __grid_constant__ KParam
         if (px < P.npx) P.out[px] = o;
     }
 }
+
+size_t fwd_smem_bytes(int threads) { return sizeof(Tables) + (size_t)(threads / 32) * sizeof(WarpQueue); }
 
 // --------------------------------------------------------------------------
 // parity trace: one thread per listed pixel, every evaluation recorded
@@ -234,7 +236,17 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ KPar
 }
 
 cudaError_t launch_fwd(const KParams& P, cudaStream_t s, FwdLaunch cfg) {
-    fwd_kernel<<<cfg.blocks, cfg.threads, 0, s>>>(P);
+    const size_t smem = fwd_smem_bytes(cfg.threads);
+    static thread_local int configured_for = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_for != dev) {
+        const cudaError_t e = cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)fwd_smem_bytes(1024));
+        if (e != cudaSuccess) return e;
+        configured_for = dev;
+    }
+    fwd_kernel<<<cfg.blocks, cfg.threads, smem, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -40,8 +40,9 @@ def _check_plane(t, name, shape_tail, device=None, host=False):
 
 def render(gbuf: torch.Tensor, light_px: Optional[torch.Tensor] = None, mat_px: Optional[torch.Tensor] = None,
            material: Material = Material(), lights: Sequence[Light] = (), out: Optional[torch.Tensor] = None,
-           stream=None) -> torch.Tensor:
-    """Glint radiance [H, W] of one G-buffer frame (glint_eval)."""
+           stream=None, launch=None) -> torch.Tensor:
+    """Glint radiance [H, W] of one G-buffer frame (glint_eval; with
+    launch = (threads_per_cta, ctas_per_sm), glint_eval_launch)."""
     _check_plane(gbuf, "gbuf", (16,))
     dev = gbuf.device
     H, W = int(gbuf.shape[0]), int(gbuf.shape[1])
@@ -54,14 +55,19 @@ def render(gbuf: torch.Tensor, light_px: Optional[torch.Tensor] = None, mat_px: 
     mat = _lib.material_struct(material)
     lts = _lib.lights_struct(lights)
     with torch.cuda.device(dev):
-        rc = _lib.lib().glint_eval(C.byref(frame), C.byref(mat), lts, out.data_ptr(), _stream_handle(stream))
+        if launch is None:
+            rc = _lib.lib().glint_eval(C.byref(frame), C.byref(mat), lts, out.data_ptr(), _stream_handle(stream))
+        else:
+            cfg = _lib.GlintLaunch(int(launch[0]), int(launch[1]))
+            rc = _lib.lib().glint_eval_launch(C.byref(frame), C.byref(mat), lts, out.data_ptr(), C.byref(cfg),
+                                              _stream_handle(stream))
     _lib.check(rc, "glint_eval")
     return out
 
 
-def render_scene(scene: Scene, out=None, stream=None, material=None, lights=None) -> torch.Tensor:
+def render_scene(scene: Scene, out=None, stream=None, material=None, lights=None, launch=None) -> torch.Tensor:
     return render(scene.gbuf, scene.light_px, scene.mat_px, material or scene.material,
-                  scene.lights if lights is None else lights, out=out, stream=stream)
+                  scene.lights if lights is None else lights, out=out, stream=stream, launch=launch)
 
 
 def staging_bytes(scene: Scene) -> int:
