@@ -182,6 +182,49 @@ def run_ours(args, rank, world, dev):
                 bytes=frame_bytes(scd))
 
 
+def run_batched(args, dev):
+    """64-frame camera orbit of the sphere scene at mixed resolutions (16 each
+    of 256^2, 512^2, 1280x720, 1920x1080): one persistent launch replayed
+    from a CUDA graph, against 64 plain glint_eval launches."""
+    from paper_2306_05051_gb300 import glint, scenes
+    frames = scenes.orbit_frames(64, device=dev)
+    npx = sum(f.width * f.height for f in frames)
+    outs = [torch.empty(f.height, f.width, dtype=torch.float32, device=dev) for f in frames]
+    stream = torch.cuda.Stream(device=dev)
+    ctx = glint.BatchContext(dev)
+    ctx.render(frames, outs=outs, stream=stream)          # autotune + record the graph
+    steps = max(3, min(args.steps, 20))
+    for _ in range(args.warmup):
+        ctx.render(frames, outs=outs, stream=stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        ctx.render(frames, outs=outs, stream=stream)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_b = ev0.elapsed_time(ev1) / steps
+    for _ in range(args.warmup):
+        for f, o in zip(frames, outs):
+            glint.render_scene(f, out=o, stream=stream)
+    stream.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        for f, o in zip(frames, outs):
+            glint.render_scene(f, out=o, stream=stream)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_p = ev0.elapsed_time(ev1) / steps
+    launch = ctx.launch
+    ctx.close()
+    return {"workload": "orbit of the sphere scene, 64 frames (16 each of 256x256, 512x512, 1280x720, "
+                        "1920x1080), 2 point lights, per-pixel material",
+            "pixels": npx, "value": npx / (ms_b * 1e-3) / 1e9, "unit": "Gpixel/s", "ms_per_batch": ms_b,
+            "plain_value": npx / (ms_p * 1e-3) / 1e9, "plain_ms_per_batch": ms_p,
+            "speedup_vs_plain": ms_p / ms_b, "launch": launch, "graph_launches_per_batch": 1,
+            "plain_launches_per_batch": len(frames)}
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle on the host cores on a deterministic row sample of the
     same 4K frame (every 64th row, then further rows until ~seconds)."""
@@ -212,6 +255,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -273,6 +317,8 @@ def main():
         "clocks": r["clocks"],
         "census": cen,
     }
+    if not args.no_batched:
+        line["batched"] = run_batched(args, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -149,6 +149,36 @@ int glint_eval_host(const GlintFrame* host_frame, const GlintMaterial* material,
                     const GlintLight* lights, float* out_host,
                     void* staging, size_t staging_bytes, void* stream);
 
+/* Batched evaluation: many frames (each with its own planes, size and
+ * n_lights; one material and one light array for all) shaded by ONE
+ * persistent kernel whose CTAs take 1-tile work items from a counter, so
+ * frames of uneven size and cost balance across the GPU.  The launch is
+ * recorded in a CUDA graph (counter reset + kernel) owned by the context and
+ * replayed on later calls; a new set of frame pointers only updates the
+ * graph's kernel node.  Results are bit-identical to glint_eval per frame.
+ *
+ * Context: created on the current device; owns a 4-byte device counter, an
+ * internal stream and the graph.  Not thread-safe; batches of one context
+ * must not run concurrently on the GPU (use one stream per context).
+ *
+ * glint_eval_batch: frames (host array of n_frames <= 128), outs (host array
+ * of n_frames device pointers, [height][width] floats each).  The first call
+ * for a given batch shape (sizes, light counts, planes present) times the
+ * candidate launch shapes on the context's stream, which blocks the host
+ * until they finish and writes the outputs several times; later calls with
+ * the same shape are asynchronous graph launches on `stream`.  Unless the
+ * launch shape was set with glint_ctx_set_launch, a new batch shape re-tunes.
+ * Errors: GLINT_ERR_ARG (bad counts, frames, material, or a context of
+ * another device), GLINT_ERR_ALIGN, GLINT_ERR_NOT_DEVICE_PTR, GLINT_ERR_CUDA. */
+typedef struct GlintContext GlintContext;
+int glint_ctx_create(GlintContext** ctx);
+void glint_ctx_destroy(GlintContext* ctx);
+int glint_ctx_get_launch(const GlintContext* ctx, GlintLaunch* launch);
+int glint_ctx_set_launch(GlintContext* ctx, const GlintLaunch* launch);
+int glint_eval_batch(GlintContext* ctx, const GlintFrame* frames, int32_t n_frames,
+                     const GlintMaterial* material, const GlintLight* lights,
+                     float* const* outs, void* stream);
+
 /* Parity trace of selected pixels: for each listed pixel, a summary and the
  * records of every binomial evaluation in the canonical order (light,
  * sub-footprint, tetrahedron vertex 0..3, simplex vertex 0..2, angular

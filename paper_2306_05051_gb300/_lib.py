@@ -62,6 +62,11 @@ SIGNATURES = {
     "glint_eval_host_staging_size": (C.c_size_t, [C.c_int32] * 5),
     "glint_eval_host": (C.c_int, [_P, _P, _P, _P, _P, C.c_size_t, _P]),
     "glint_eval_trace": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, C.c_int32, _P]),
+    "glint_ctx_create": (C.c_int, [_P]),
+    "glint_ctx_destroy": (None, [_P]),
+    "glint_ctx_get_launch": (C.c_int, [_P, _P]),
+    "glint_ctx_set_launch": (C.c_int, [_P, _P]),
+    "glint_eval_batch": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P]),
 }
 
 

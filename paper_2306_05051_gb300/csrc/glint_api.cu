@@ -68,6 +68,8 @@ int check_material(const GlintMaterial* m) {
     return GLINT_OK;
 }
 
+}  // namespace
+
 int check_frame_shape(const GlintFrame* f, const GlintLight* lights) {
     if (!f || !f->gbuf) return GLINT_ERR_ARG;
     if (f->width <= 0 || f->height <= 0) return GLINT_ERR_ARG;
@@ -98,6 +100,7 @@ int check_device_ptr(const void* p, size_t align) {
     return GLINT_OK;
 }
 
+namespace {
 std::mutex g_dev_mutex;
 int g_sm_count[64];
 constexpr int kDefaultThreads = 512;
@@ -120,18 +123,12 @@ int num_sms() {
 
 size_t tables_bytes(int M) { return sizeof(DfTables) + (size_t)rot_entries(M) * sizeof(RotEntry); }
 
-int make_params(const GlintFrame* f, const GlintMaterial* m, const GlintLight* lights, float* out, KParams* P) {
-    int rc = check_material(m);
+int make_material_params(const GlintMaterial* m, const GlintLight* lights, int n_lights, KParams* P) {
+    const int rc = check_material(m);
     if (rc) return rc;
-    rc = check_frame_shape(f, lights);
-    if (rc) return rc;
+    if (n_lights < 0 || n_lights > GLINT_MAX_LIGHTS || (n_lights > 0 && !lights)) return GLINT_ERR_ARG;
     std::memset(P, 0, sizeof(KParams));
-    P->gbuf = reinterpret_cast<const float4*>(f->gbuf);
-    P->light_px = reinterpret_cast<const float4*>(f->light_px);
-    P->mat_px = reinterpret_cast<const float2*>(f->mat_px);
-    P->out = out;
-    P->W = f->width; P->H = f->height; P->npx = f->width * f->height; P->nL = f->n_lights;
-    for (int l = 0; l < f->n_lights; ++l) {
+    for (int l = 0; l < n_lights; ++l) {
         P->lights[l].kind = lights[l].kind;
         P->lights[l].dx = lights[l].dir[0]; P->lights[l].dy = lights[l].dir[1]; P->lights[l].dz = lights[l].dir[2];
         P->lights[l].E = lights[l].intensity;
@@ -146,6 +143,26 @@ int make_params(const GlintFrame* f, const GlintMaterial* m, const GlintLight* l
     P->top = (float)std::pow((double)m->lod_factor, m->n_lods - 1);
     P->log2f = m->lod_factor == 4 ? 2 : 1;
     std::memcpy(&P->tables, &host_tables(), sizeof(Tables));
+    return GLINT_OK;
+}
+
+FrameDesc make_frame_desc(const GlintFrame* f, float* out) {
+    FrameDesc F;
+    F.gbuf = reinterpret_cast<const float4*>(f->gbuf);
+    F.light_px = reinterpret_cast<const float4*>(f->light_px);
+    F.mat_px = reinterpret_cast<const float2*>(f->mat_px);
+    F.out = out;
+    F.W = f->width; F.H = f->height; F.npx = f->width * f->height; F.nL = f->n_lights;
+    return F;
+}
+
+// Single-frame parameters: material + frame, all host-side checks.
+static int make_params(const GlintFrame* f, const GlintMaterial* m, const GlintLight* lights, float* out,
+                       KParams* P, FrameDesc* F) {
+    int rc = check_frame_shape(f, lights);
+    if (rc) return rc;
+    if ((rc = make_material_params(m, lights, f->n_lights, P))) return rc;
+    *F = make_frame_desc(f, out);
     return GLINT_OK;
 }
 
@@ -202,21 +219,23 @@ int glint_eval_launch(const GlintFrame* frame, const GlintMaterial* material, co
     if ((t != 128 && t != 256 && t != 512 && t != 1024) || launch->ctas_per_sm < 1 || launch->ctas_per_sm > 16)
         return GLINT_ERR_ARG;
     KParams P;
-    int rc = make_params(frame, material, lights, out, &P);
+    FrameDesc F;
+    int rc = make_params(frame, material, lights, out, &P, &F);
     if (rc) return rc;
     if ((rc = check_frame_device(frame, lights))) return rc;
     if ((rc = check_device_ptr(out, 4))) return rc;
-    return cuda_rc(launch_fwd(P, (cudaStream_t)stream, make_fwd_launch(P.npx, t, launch->ctas_per_sm)));
+    return cuda_rc(launch_fwd(P, F, (cudaStream_t)stream, make_fwd_launch(F.npx, t, launch->ctas_per_sm)));
 }
 
 int glint_eval(const GlintFrame* frame, const GlintMaterial* material, const GlintLight* lights, float* out,
                void* stream) {
     KParams P;
-    int rc = make_params(frame, material, lights, out, &P);
+    FrameDesc F;
+    int rc = make_params(frame, material, lights, out, &P, &F);
     if (rc) return rc;
     if ((rc = check_frame_device(frame, lights))) return rc;
     if ((rc = check_device_ptr(out, 4))) return rc;
-    return cuda_rc(launch_fwd(P, (cudaStream_t)stream, default_fwd_launch(P.npx)));
+    return cuda_rc(launch_fwd(P, F, (cudaStream_t)stream, default_fwd_launch(F.npx)));
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -262,8 +281,9 @@ int glint_eval_host(const GlintFrame* hf, const GlintMaterial* material, const G
     }
     float* dout = reinterpret_cast<float*>(base + off);
     KParams P;
-    if ((rc = make_params(&df_, material, lights, dout, &P))) return rc;
-    if ((rc = cuda_rc(launch_fwd(P, s, default_fwd_launch(P.npx))))) return rc;
+    FrameDesc F;
+    if ((rc = make_params(&df_, material, lights, dout, &P, &F))) return rc;
+    if ((rc = cuda_rc(launch_fwd(P, F, s, default_fwd_launch(F.npx))))) return rc;
     if (cudaMemcpyAsync(out_host, dout, npx * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return GLINT_ERR_CUDA;
     return GLINT_OK;
 }
@@ -273,12 +293,13 @@ int glint_eval_trace(const GlintFrame* frame, const GlintMaterial* material, con
                      void* stream) {
     if (n_px <= 0 || rec_cap < 0) return GLINT_ERR_ARG;
     KParams P;
-    int rc = make_params(frame, material, lights, nullptr, &P);
+    FrameDesc F;
+    int rc = make_params(frame, material, lights, nullptr, &P, &F);
     if (rc) return rc;
     if ((rc = check_frame_device(frame, lights))) return rc;
     if ((rc = check_device_ptr(px, 4)) || (rc = check_device_ptr(pix, 4))) return rc;
     if (rec_cap > 0 && (rc = check_device_ptr(recs, 4))) return rc;
-    return cuda_rc(launch_trace(P, px, n_px, pix, recs, rec_cap, (cudaStream_t)stream));
+    return cuda_rc(launch_trace(P, F, px, n_px, pix, recs, rec_cap, (cudaStream_t)stream));
 }
 
 }  // extern "C"

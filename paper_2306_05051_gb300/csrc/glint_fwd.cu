@@ -70,17 +70,18 @@ struct LightEval {          // what the evaluation loop needs of one light
 };
 
 // Shade the pixel of this lane (px valid or not); all 32 lanes call together.
-__device__ float shade_warp(const KParams& P, const Tables& T, WarpQueue& q, int px, bool valid) {
+__device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& F, WarpQueue& q, int px,
+                            bool valid) {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     PixelSetup S;
     S.status = 1;
     S.K = 0;
-    if (valid) setup_pixel(P, T, px, S);
+    if (valid) setup_pixel(P, T, F, px, S);
     LightState ls[kMaxLights];
-    for (int l = 0; l < P.nL; ++l) {
+    for (int l = 0; l < F.nL; ++l) {
         ls[l].on = false;
-        if (S.status == 0) setup_light(P, S, px, l, ls[l]);
+        if (S.status == 0) setup_light(P, F, S, px, l, ls[l]);
     }
     const int K = S.status == 0 ? S.K : 0;
     const int Kw = __reduce_max_sync(0xffffffffu, K);
@@ -95,7 +96,7 @@ __device__ float shade_warp(const KParams& P, const Tables& T, WarpQueue& q, int
             act = in_range;
         }
 #pragma unroll 1
-        for (int l = 0; l < P.nL; ++l) {
+        for (int l = 0; l < F.nL; ++l) {
             LightEval L;
             L.on = act && ls[l].on;
             L.p = ls[l].p; L.shade = ls[l].shade;
@@ -143,7 +144,7 @@ __device__ float shade_warp(const KParams& P, const Tables& T, WarpQueue& q, int
     return acc / S.A.hi;
 }
 
-__global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KParams P) {
+__global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KParams P, const FrameDesc F) {
     extern __shared__ __align__(16) unsigned char smem[];
     Tables& T = *reinterpret_cast<Tables*>(smem);
     WarpQueue* Qs = reinterpret_cast<WarpQueue*>(smem + sizeof(Tables));
@@ -152,11 +153,40 @@ __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KPara
     // Block-uniform tiles of blockDim.x pixels.  The barrier at the top of a
     // tile keeps the block's warps together in the (long, mostly
     // straight-line) setup code so they share instruction-cache lines.
-    for (int base = blockIdx.x * blockDim.x; base < P.npx; base += gridDim.x * blockDim.x) {
+    for (int base = blockIdx.x * blockDim.x; base < F.npx; base += gridDim.x * blockDim.x) {
         __syncthreads();
         const int px = base + (int)threadIdx.x;
-        const float o = shade_warp(P, T, q, px, px < P.npx);
-        if (px < P.npx) P.out[px] = o;
+        const float o = shade_warp(P, T, F, q, px, px < F.npx);
+        if (px < F.npx) F.out[px] = o;
+    }
+}
+
+// Persistent kernel over the tiles of many frames: CTAs take tiles from a
+// global counter (reset to 0 before the launch); tile t belongs to frame f
+// with tile_base[f] <= t < tile_base[f+1].
+__global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KParams P,
+                                                     const __grid_constant__ BatchDesc B) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Tables& T = *reinterpret_cast<Tables*>(smem);
+    WarpQueue* Qs = reinterpret_cast<WarpQueue*>(smem + sizeof(Tables));
+    __shared__ int tile_s;
+    load_tables(P, T);
+    WarpQueue& q = Qs[threadIdx.x >> 5];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) tile_s = (int)atomicAdd(B.counter, 1u);
+        __syncthreads();
+        const int t = tile_s;
+        if (t >= B.tile_base[B.n]) break;
+        int lo = 0, hi = B.n - 1;                 // last frame with tile_base <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.tile_base[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const FrameDesc& F = B.frames[lo];
+        const int px = (t - B.tile_base[lo]) * (int)blockDim.x + (int)threadIdx.x;
+        const float o = shade_warp(P, T, F, q, px, px < F.npx);
+        if (px < F.npx) F.out[px] = o;
     }
 }
 
@@ -165,23 +195,23 @@ size_t fwd_smem_bytes(int threads) { return sizeof(Tables) + (size_t)(threads / 
 // --------------------------------------------------------------------------
 // parity trace: one thread per listed pixel, every evaluation recorded
 // --------------------------------------------------------------------------
-__device__ void trace_pixel(const KParams& P, const Tables& T, int px, GlintTracePix* pr, GlintTraceRec* recs,
-                            int cap) {
+__device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& F, int px, GlintTracePix* pr,
+                            GlintTraceRec* recs, int cap) {
     PixelSetup S;
-    setup_pixel(P, T, px, S);
+    setup_pixel(P, T, F, px, S);
     pr->status = S.status; pr->K = S.status == 0 ? S.K : 0; pr->n_rec = 0; pr->pad = 0;
     pr->A = S.status == 0 ? S.A.hi : 0.0f; pr->r = S.status == 0 ? S.ratio.hi : 0.0f;
     pr->phi = S.status == 0 ? S.phi.hi : 0.0f; pr->out = 0.0f;
     if (S.status != 0) return;
     LightState ls[kMaxLights];
-    for (int l = 0; l < P.nL; ++l) setup_light(P, S, px, l, ls[l]);
+    for (int l = 0; l < F.nL; ++l) setup_light(P, F, S, px, l, ls[l]);
     float C[kMaxLights];
-    for (int l = 0; l < P.nL; ++l) C[l] = 0.0f;
+    for (int l = 0; l < F.nL; ++l) C[l] = 0.0f;
     int nrec = 0;
     for (int sub = 0; sub < S.K; ++sub) {
         SubState U;
         if (!setup_sub(P, T, S, sub, U)) { pr->status = 3; pr->n_rec = nrec; return; }
-        for (int l = 0; l < P.nL; ++l) {
+        for (int l = 0; l < F.nL; ++l) {
             const LightState& L = ls[l];
             if (!L.on) continue;
             for (int i = 0; i < 4; ++i) {
@@ -213,48 +243,62 @@ __device__ void trace_pixel(const KParams& P, const Tables& T, int px, GlintTrac
         }
     }
     float out = 0.0f;
-    for (int l = 0; l < P.nL; ++l)
+    for (int l = 0; l < F.nL; ++l)
         if (ls[l].on) out += ls[l].shade * C[l];
     pr->out = out / S.A.hi;
     pr->n_rec = nrec;
 }
 
-__global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ KParams P, const int32_t* px_list,
-                                                    int32_t n_px, GlintTracePix* pix, GlintTraceRec* recs,
-                                                    int32_t cap) {
+__global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ KParams P, const FrameDesc F,
+                                                    const int32_t* px_list, int32_t n_px, GlintTracePix* pix,
+                                                    GlintTraceRec* recs, int32_t cap) {
     __shared__ Tables T;
     load_tables(P, T);
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_px) return;
     const int px = px_list[k];
-    if (px < 0 || px >= P.npx) {
+    if (px < 0 || px >= F.npx) {
         pix[k].status = 2; pix[k].K = 0; pix[k].n_rec = 0; pix[k].pad = 0;
         pix[k].A = pix[k].r = pix[k].phi = pix[k].out = 0.0f;
         return;
     }
-    trace_pixel(P, T, px, pix + k, recs + (size_t)k * cap, cap);
+    trace_pixel(P, T, F, px, pix + k, recs + (size_t)k * cap, cap);
 }
 
-cudaError_t launch_fwd(const KParams& P, cudaStream_t s, FwdLaunch cfg) {
-    const size_t smem = fwd_smem_bytes(cfg.threads);
+static cudaError_t configure_smem() {
     static thread_local int configured_for = -1;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (configured_for != dev) {
-        const cudaError_t e = cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)fwd_smem_bytes(1024));
-        if (e != cudaSuccess) return e;
-        configured_for = dev;
-    }
-    fwd_kernel<<<cfg.blocks, cfg.threads, smem, s>>>(P);
+    if (configured_for == dev) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fwd_smem_bytes(1024));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem_bytes(1024));
+    if (e == cudaSuccess) configured_for = dev;
+    return e;
+}
+
+cudaError_t launch_fwd(const KParams& P, const FrameDesc& F, cudaStream_t s, FwdLaunch cfg) {
+    const cudaError_t e = configure_smem();
+    if (e != cudaSuccess) return e;
+    fwd_kernel<<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, F);
     return cudaGetLastError();
 }
 
-cudaError_t launch_trace(const KParams& P, const int32_t* px, int32_t n_px, GlintTracePix* pix,
-                         GlintTraceRec* recs, int32_t cap, cudaStream_t s) {
+cudaError_t launch_batch(const KParams& P, const BatchDesc& B, cudaStream_t s, FwdLaunch cfg) {
+    const cudaError_t e = configure_smem();
+    if (e != cudaSuccess) return e;
+    batch_kernel<<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, B);
+    return cudaGetLastError();
+}
+
+const void* batch_kernel_fn() { return reinterpret_cast<const void*>(&batch_kernel); }
+
+cudaError_t launch_trace(const KParams& P, const FrameDesc& F, const int32_t* px, int32_t n_px,
+                         GlintTracePix* pix, GlintTraceRec* recs, int32_t cap, cudaStream_t s) {
     const int threads = 128;
     const int blocks = (n_px + threads - 1) / threads;
-    trace_kernel<<<blocks, threads, 0, s>>>(P, px, n_px, pix, recs, cap);
+    trace_kernel<<<blocks, threads, 0, s>>>(P, F, px, n_px, pix, recs, cap);
     return cudaGetLastError();
 }
 

@@ -7,25 +7,41 @@
 
 namespace glint {
 
-// Launch configuration of the plain forward kernel.
+// Launch configuration of the forward kernels.
 struct FwdLaunch {
     int threads;
     int blocks;
 };
 
-// Fill every derived field of KParams from the public structs (no device work).
-int make_params(const GlintFrame* frame, const GlintMaterial* mat, const GlintLight* lights, float* out,
-                KParams* P);
+constexpr int kMaxBatch = 128;
+
+// Frames of one persistent batched launch (passed by value as a kernel
+// parameter, so a graph node can be re-pointed without re-capture).
+struct BatchDesc {
+    int32_t n;
+    uint32_t* counter;                  // tile counter, zero at launch
+    int32_t tile_base[kMaxBatch + 1];   // first tile of each frame; tile_base[n] = total
+    FrameDesc frames[kMaxBatch];
+};
+
+// Material, lights (n of them) and tables into KParams (host only).
+int make_material_params(const GlintMaterial* mat, const GlintLight* lights, int n_lights, KParams* P);
+// Shape checks of a frame (host only).
+int check_frame_shape(const GlintFrame* f, const GlintLight* lights);
+FrameDesc make_frame_desc(const GlintFrame* f, float* out);
 // Validate a frame's device pointers (null, alignment, device accessibility).
 int check_frame_device(const GlintFrame* frame, const GlintLight* lights);
+int check_device_ptr(const void* p, size_t align);
 int num_sms();
+int cuda_rc(cudaError_t e);
 
-cudaError_t launch_fwd(const KParams& P, cudaStream_t s, FwdLaunch cfg);
+cudaError_t launch_fwd(const KParams& P, const FrameDesc& F, cudaStream_t s, FwdLaunch cfg);
+cudaError_t launch_batch(const KParams& P, const BatchDesc& B, cudaStream_t s, FwdLaunch cfg);
+const void* batch_kernel_fn();
 size_t fwd_smem_bytes(int threads);
 FwdLaunch default_fwd_launch(int npx);
 FwdLaunch make_fwd_launch(int npx, int threads, int ctas_per_sm);
-cudaError_t launch_trace(const KParams& P, const int32_t* px, int32_t n_px, GlintTracePix* pix,
-                         GlintTraceRec* recs, int32_t cap, cudaStream_t s);
-size_t tables_bytes(int M);
+cudaError_t launch_trace(const KParams& P, const FrameDesc& F, const int32_t* px, int32_t n_px,
+                         GlintTracePix* pix, GlintTraceRec* recs, int32_t cap, cudaStream_t s);
 
 }  // namespace glint

@@ -51,12 +51,17 @@ struct KLight {
     float dx, dy, dz, E;
 };
 
-struct KParams {
+// One frame's planes (device pointers) and size.
+struct FrameDesc {
     const float4* gbuf;
     const float4* light_px;
     const float2* mat_px;
     float* out;
     int32_t W, H, npx, nL;
+};
+
+// Material, lights and tables, shared by every frame of a launch.
+struct KParams {
     KLight lights[kMaxLights];
     int32_t ndf;
     float ax, ay;
@@ -168,8 +173,8 @@ struct PixelSetup {
     float ax, ay, cos_v, lam_v;
 };
 
-__device__ __forceinline__ bool load_gbuf(const KParams& P, int px, float4& g0, float4& g1, float4& g2, float4& g3) {
-    const float4* g = P.gbuf + (size_t)px * 4;
+__device__ __forceinline__ bool load_gbuf(const FrameDesc& F, int px, float4& g0, float4& g1, float4& g2, float4& g3) {
+    const float4* g = F.gbuf + (size_t)px * 4;
     g0 = __ldg(g); g1 = __ldg(g + 1); g2 = __ldg(g + 2); g3 = __ldg(g + 3);
     const float gv[15] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z};
     bool finite = true;
@@ -178,11 +183,12 @@ __device__ __forceinline__ bool load_gbuf(const KParams& P, int px, float4& g0, 
     return finite;
 }
 
-static __device__ __noinline__ void setup_pixel(const KParams& P, const Tables& T, int px, PixelSetup& S) {
+static __device__ __noinline__ void setup_pixel(const KParams& P, const Tables& T, const FrameDesc& F, int px,
+                                               PixelSetup& S) {
     S.status = 2;
     S.K = 0;
     float4 g0, g1, g2, g3;
-    if (!load_gbuf(P, px, g0, g1, g2, g3)) return;
+    if (!load_gbuf(F, px, g0, g1, g2, g3)) return;
 
     // ---- 1. shading frame (double-float: the angular texel coordinate
     //      h_t / gamma amplifies FP32 rounding of the frame ~20x) ----------
@@ -218,8 +224,8 @@ static __device__ __noinline__ void setup_pixel(const KParams& P, const Tables& 
     df rho = ldf(P.rho);
     S.srho = ldf(P.sqrt_rho);
     S.ax = P.ax; S.ay = P.ay;
-    if (P.mat_px) {
-        const float2 mp = __ldg(P.mat_px + px);
+    if (F.mat_px) {
+        const float2 mp = __ldg(F.mat_px + px);
         S.ax = S.ay = mp.x;
         rho = mkdf(mp.y);
         S.srho = dfsqrt(rho);
@@ -236,19 +242,19 @@ static __device__ __noinline__ void setup_pixel(const KParams& P, const Tables& 
         const float s = pow2f(-je);
         ja *= s; jb *= s; jc *= s; jd *= s;
     }
-    const df E = two_prod(ja, ja) + two_prod(jb, jb);
-    const df G = two_prod(jc, jc) + two_prod(jd, jd);
-    const df F = two_prod(ja, jc) + two_prod(jb, jd);
+    const df jE = two_prod(ja, ja) + two_prod(jb, jb);
+    const df jG = two_prod(jc, jc) + two_prod(jd, jd);
+    const df jF = two_prod(ja, jc) + two_prod(jb, jd);
     const df det = dfabs(two_prod(ja, jd) - two_prod(jc, jb));
     const df Pft = scale2(det, 2 * je);                 // |det J| in uv^2
     S.A = Pft * rho;                                    // flakes in the footprint
     if (!(S.A.hi > 0.0f)) return;
-    const df hm = scale2(E - G, -1);
-    const df hyp = dfsqrt(hm * hm + F * F);
-    const df s0sq = scale2(E + G, -1) + hyp;
+    const df hm = scale2(jE - jG, -1);
+    const df hyp = dfsqrt(hm * hm + jF * jF);
+    const df s0sq = scale2(jE + jG, -1) + hyp;
     // ratio sigma0 / max(sigma1, 2^-20 sigma0): finite for line-like footprints
     S.ratio = dflt(s0sq, scale2(det, 20)) ? s0sq / det : mkdf(1048576.0f);
-    S.phi = scale2(dfatan2(scale2(F, 1), E - G, T.d), -1);
+    S.phi = scale2(dfatan2(scale2(jF, 1), jE - jG, T.d), -1);
     if (dfsign(S.phi) < 0) S.phi = S.phi + ldf(T.d.pi);
     if (!dflt(S.phi, ldf(T.d.pi))) S.phi = S.phi - ldf(T.d.pi);
     S.u = mkdf(g0.x); S.v = mkdf(g0.y);
@@ -273,7 +279,7 @@ static __device__ __noinline__ void setup_pixel(const KParams& P, const Tables& 
         // major axis u0 of the footprint (eigenvector of J J^T for sigma0^2),
         // oriented like (cos phi, sin phi) with phi in [0, pi)
         df ex, ey;
-        if (dfsign(hm) >= 0) { ex = hyp + hm; ey = F; } else { ex = F; ey = hyp - hm; }
+        if (dfsign(hm) >= 0) { ex = hyp + hm; ey = jF; } else { ex = jF; ey = hyp - hm; }
         if (ex.hi == 0.0f && ey.hi == 0.0f) ex = mkdf(1.0f);
         const df inv = dfrsqrt(ex * ex + ey * ey);
         S.u0x = ex * inv; S.u0y = ey * inv;
@@ -373,12 +379,13 @@ struct LightState {
     int32_t ax[4], ay[4];         // angular texels (traces)
 };
 
-static __device__ __noinline__ void setup_light(const KParams& P, const PixelSetup& S, int px, int l, LightState& L) {
+static __device__ __noinline__ void setup_light(const KParams& P, const FrameDesc& F, const PixelSetup& S, int px, int l,
+                                               LightState& L) {
     L.on = false;
     const KLight kl = P.lights[l];
     float lr[3], E;
     if (kl.kind == 0) {
-        const float4 lp = __ldg(P.light_px + (size_t)l * P.npx + px);
+        const float4 lp = __ldg(F.light_px + (size_t)l * F.npx + px);
         lr[0] = lp.x; lr[1] = lp.y; lr[2] = lp.z; E = lp.w;
     } else {
         lr[0] = kl.dx; lr[1] = kl.dy; lr[2] = kl.dz; E = kl.E;

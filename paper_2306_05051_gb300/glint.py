@@ -120,3 +120,61 @@ def trace(scene: Scene, pixels, cap: Optional[int] = None, stream=None, material
     p = pix.cpu().numpy().view(_lib.TRACE_PIX_DTYPE)
     r = recs.cpu().numpy().view(_lib.TRACE_REC_DTYPE).reshape(n, cap)
     return p, r
+
+
+class BatchContext:
+    """Batched evaluation context (glint_ctx_* / glint_eval_batch): one
+    persistent launch over many frames, recorded in a CUDA graph and
+    replayed; the launch shape is tuned on the first batch of a shape."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.lib().glint_ctx_create(C.byref(self._h)), "glint_ctx_create")
+
+    def close(self):
+        if self._h:
+            _lib.lib().glint_ctx_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launch(self):
+        L = _lib.GlintLaunch()
+        rc = _lib.lib().glint_ctx_get_launch(self._h, C.byref(L))
+        return None if rc else (int(L.threads_per_cta), int(L.ctas_per_sm))
+
+    @launch.setter
+    def launch(self, value):
+        L = _lib.GlintLaunch(int(value[0]), int(value[1]))
+        _lib.check(_lib.lib().glint_ctx_set_launch(self._h, C.byref(L)), "glint_ctx_set_launch")
+
+    def render(self, scenes_list, outs=None, stream=None, material=None, lights=None):
+        """Shade every scene (same material and light descriptors) into outs
+        (list of [H, W] device tensors, allocated when None)."""
+        n = len(scenes_list)
+        first = scenes_list[0]
+        material = material or first.material
+        lights = first.lights if lights is None else lights
+        if outs is None:
+            outs = [torch.empty(s.height, s.width, dtype=torch.float32, device=self.device) for s in scenes_list]
+        frames = (_lib.GlintFrame * n)()
+        for k, s in enumerate(scenes_list):
+            _check_plane(s.gbuf, "gbuf", (16,), self.device)
+            _check_plane(s.light_px, "light_px", (s.height, s.width, 4), self.device)
+            _check_plane(s.mat_px, "mat_px", (s.height, s.width, 2), self.device)
+            _check_plane(outs[k], "out", (s.height, s.width), self.device)
+            frames[k] = _lib.frame_struct(s.gbuf, s.light_px, s.mat_px, len(lights))
+        optr = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+        mat = _lib.material_struct(material)
+        lts = _lib.lights_struct(lights)
+        with torch.cuda.device(self.device):
+            rc = _lib.lib().glint_eval_batch(self._h, frames, n, C.byref(mat), lts, optr, _stream_handle(stream))
+        _lib.check(rc, "glint_eval_batch")
+        return outs
