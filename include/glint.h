@@ -179,6 +179,30 @@ int glint_eval_batch(GlintContext* ctx, const GlintFrame* frames, int32_t n_fram
                      const GlintMaterial* material, const GlintLight* lights,
                      float* const* outs, void* stream);
 
+/* glint_eval_batch for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is an interface for hosts that own every
+ * allocation - a renderer with a fixed memory budget, code that must not
+ * synchronise the device in the middle of a frame (cudaMalloc can), or a
+ * plug-in inside an application with its own allocator.  Same frames,
+ * material, lights and outputs as glint_eval_batch (bit-identical images),
+ * but no context, no CUDA graph, no tuning (fixed 256 threads x 4 CTAs per
+ * SM) and no allocation of any kind: the persistent kernel's tile counters
+ * live in a static 256-byte device array that every GPU loading the library
+ * keeps until the process exits.  Batches are cut into launches of up to 128
+ * frames, one counter each, so n_frames may be at most 8192; more returns
+ * GLINT_ERR_WORKSPACE before anything is enqueued.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, once per device, with that device current); make
+ *     that first call before any stream capture.
+ *   - Every call uses the same array and clears the counters it needs at the
+ *     start (an asynchronous memset on `stream`).  Calls whose work overlaps
+ *     on the GPU - on different streams, or from different threads - race on
+ *     the counters and give wrong images: order them on one stream.
+ * Errors: as glint_eval_batch, plus GLINT_ERR_WORKSPACE. */
+int glint_eval_batch_noalloc(const GlintFrame* frames, int32_t n_frames,
+                             const GlintMaterial* material, const GlintLight* lights,
+                             float* const* outs, void* stream);
+
 /* Parity trace of selected pixels: for each listed pixel, a summary and the
  * records of every binomial evaluation in the canonical order (light,
  * sub-footprint, tetrahedron vertex 0..3, simplex vertex 0..2, angular
