@@ -179,6 +179,28 @@ int glint_eval_batch(GlintContext* ctx, const GlintFrame* frames, int32_t n_fram
                      const GlintMaterial* material, const GlintLight* lights,
                      float* const* outs, void* stream);
 
+/* Adjoint (spec differentiation of the counting law, Sec. 3-6):
+ *   grad[k] = sum_px grad_out[px] * d relaxed(px) / d theta_k,
+ * theta = (alpha_x, alpha_y, ln_density, dir of light 0 (xyz), dir of light 1,
+ * ...), 3 + 3 * n_lights floats; the direction entries of point lights are 0.
+ * relaxed(px) is the image with every open gate counting
+ * clamp(1 + mu + sigma z, 1, ceil n) instead of its floor; every discrete
+ * choice (sub-footprints, LOD, cell, tetrahedron, lattice vertices, texels,
+ * gates) is held fixed; interpolation weights are differentiated.  The
+ * forward pass is recomputed per pixel (no stored per-texel state).
+ *   grad_out:    device [height][width] float.
+ *   grad:        device, 3 + 3 * n_lights floats (written).
+ *   out_relaxed: device [height][width] float or NULL (the relaxed image).
+ *   workspace:   device, >= glint_backward_workspace_size(frame) bytes,
+ *                8-byte aligned; per-CTA partial sums (deterministic
+ *                fixed-order reduction).
+ * Requires the scalar material (frame->mat_px == NULL), else
+ * GLINT_ERR_UNSUPPORTED; a small workspace gives GLINT_ERR_WORKSPACE. */
+size_t glint_backward_workspace_size(const GlintFrame* frame);
+int glint_backward(const GlintFrame* frame, const GlintMaterial* material, const GlintLight* lights,
+                   const float* grad_out, float* grad, float* out_relaxed,
+                   void* workspace, size_t workspace_bytes, void* stream);
+
 /* glint_eval_batch for callers that cannot allocate device memory.  The paper
  * has no counterpart: this is an interface for hosts that own every
  * allocation - a renderer with a fixed memory budget, code that must not

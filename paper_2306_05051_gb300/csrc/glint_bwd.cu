@@ -1,0 +1,323 @@
+// Adjoint of the glint image with respect to the material roughness
+// (alpha_x, alpha_y), ln(flake density) and the direction of each
+// directional light.
+//
+// The gradient is that of the relaxed image: an open gate contributes
+// clamp(1 + mu + sigma z, 1, ceil n) instead of its floor, and every discrete
+// choice (sub-footprints, LOD bracket, cell, triangle, tetrahedron, lattice
+// vertices, angular texels, gates) is held fixed.  The forward pass is
+// recomputed per pixel with the same setup code as the image kernels; no
+// per-texel state is stored.  Within a cell the interpolation weights are
+// differentiated in difference form, e.g. for the simplex weights
+//   sum_j du_j X_j = (qx/2)(X1 - X0) + (qy/2)(X2 - X1)   (d q / d ln rho = q/2),
+// which avoids cancelling the large +-q/2 terms.  Per-thread gradients are
+// accumulated in FP64, reduced per CTA in a fixed order into the workspace,
+// and a second kernel sums the CTA partials in a fixed order: deterministic.
+#include "glint_kernels.cuh"
+
+namespace glint {
+
+constexpr int kBwdThreads = 256;
+constexpr int kMaxGrad = 3 + 3 * kMaxLights;
+
+// Derivatives of one light's per-pixel quantities.
+struct LightGrad {
+    bool dir;                     // directional light: its direction is a parameter
+    float fx, fy;                 // angular fractions
+    float dp_da[2], dp_dd[3];     // p with respect to (alpha_x, alpha_y) and the light direction
+    float dfx_dd[3], dfy_dd[3];   // angular fractions with respect to the light direction
+    float ds_da[2], ds_dd[3];     // shade factor with respect to the same
+};
+
+__device__ __forceinline__ float dlambda_da(int ndf, float a) {
+    if (ndf == 0) return -expf(-a * a) / (3.5449077018110318f * a * a);       // 2 sqrt(pi)
+    return -0.5f / (a * a * a * sqrtf(1.0f + 1.0f / (a * a)));
+}
+
+// Lambda of w (local frame) and its derivatives with respect to (alpha_x,
+// alpha_y) and to w.
+__device__ __forceinline__ float lambda_grad(int ndf, float ax, float ay, const float w[3], float dl_da[2],
+                                             float dl_dw[3]) {
+    const float s2 = (w[0] * ax) * (w[0] * ax) + (w[1] * ay) * (w[1] * ay);
+    dl_da[0] = dl_da[1] = dl_dw[0] = dl_dw[1] = dl_dw[2] = 0.0f;
+    if (!(s2 > 0.0f)) return 0.0f;
+    const float sq = sqrtf(s2);
+    const float a = w[2] / sq;
+    const float lam = smith_lambda(ndf, ax, ay, w[0], w[1], w[2]);
+    const float dla = dlambda_da(ndf, a);
+    dl_da[0] = dla * (-a * w[0] * w[0] * ax / s2);
+    dl_da[1] = dla * (-a * w[1] * w[1] * ay / s2);
+    dl_dw[0] = dla * (-a * w[0] * ax * ax / s2);
+    dl_dw[1] = dla * (-a * w[1] * ay * ay / s2);
+    dl_dw[2] = dla / sq;
+    return lam;
+}
+
+__device__ void light_grad(const KParams& P, const FrameDesc& F, const PixelSetup& S, int px, int l,
+                           const LightState& L, LightGrad& G) {
+    const KLight kl = P.lights[l];
+    G.dir = kl.kind == 1;
+    float d[3];
+    if (kl.kind == 0) {
+        const float4 lp = __ldg(F.light_px + (size_t)l * F.npx + px);
+        d[0] = lp.x; d[1] = lp.y; d[2] = lp.z;
+    } else {
+        d[0] = kl.dx; d[1] = kl.dy; d[2] = kl.dz;
+    }
+    const float dl = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const float w[3] = {d[0] / dl, d[1] / dl, d[2] / dl};
+    float Fr[3][3];
+    for (int c = 0; c < 3; ++c) { Fr[0][c] = S.tg[c].hi; Fr[1][c] = S.b[c].hi; Fr[2][c] = S.n[c].hi; }
+    float ll[3], v[3];
+    for (int r = 0; r < 3; ++r) { ll[r] = Fr[r][0] * w[0] + Fr[r][1] * w[1] + Fr[r][2] * w[2]; v[r] = S.wv[r].hi; }
+    float hs[3] = {v[0] + ll[0], v[1] + ll[1], v[2] + ll[2]};
+    const float hl = sqrtf(hs[0] * hs[0] + hs[1] * hs[1] + hs[2] * hs[2]);
+    const float h[3] = {hs[0] / hl, hs[1] / hl, hs[2] / hl};
+    // local light direction and half-vector with respect to the world direction d
+    float Jl[3][3], Jh[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) Jl[r][c] = (Fr[r][c] - ll[r] * w[c]) / dl;
+    for (int c = 0; c < 3; ++c) {
+        const float hj = h[0] * Jl[0][c] + h[1] * Jl[1][c] + h[2] * Jl[2][c];
+        for (int r = 0; r < 3; ++r) Jh[r][c] = (Jl[r][c] - h[r] * hj) / hl;
+    }
+    const float ax = S.ax, ay = S.ay, ht = h[0], hb = h[1], hn = h[2];
+    // Eq. 4: p = R D(h)/D(n)
+    const float e = (ht / ax) * (ht / ax) + (hb / ay) * (hb / ay);
+    float dr_dh[3], dr_da[2];
+    if (P.ndf == 0) {
+        const float hn2 = hn * hn;
+        const float rat = expf(-e / hn2) / (hn2 * hn2);
+        dr_dh[0] = rat * (-2.0f * ht / (ax * ax * hn2));
+        dr_dh[1] = rat * (-2.0f * hb / (ay * ay * hn2));
+        dr_dh[2] = rat * (2.0f * e / (hn2 * hn) - 4.0f / hn);
+        dr_da[0] = rat * (2.0f * ht * ht / (ax * ax * ax * hn2));
+        dr_da[1] = rat * (2.0f * hb * hb / (ay * ay * ay * hn2));
+    } else {
+        const float Dd = e + hn * hn;
+        const float k = -2.0f / (Dd * Dd * Dd);
+        dr_dh[0] = k * 2.0f * ht / (ax * ax);
+        dr_dh[1] = k * 2.0f * hb / (ay * ay);
+        dr_dh[2] = k * 2.0f * hn;
+        dr_da[0] = k * (-2.0f * ht * ht / (ax * ax * ax));
+        dr_da[1] = k * (-2.0f * hb * hb / (ay * ay * ay));
+    }
+    const bool clamped = !(L.p < 1.0f);
+    for (int c = 0; c < 2; ++c) G.dp_da[c] = clamped ? 0.0f : P.R * dr_da[c];
+    for (int c = 0; c < 3; ++c)
+        G.dp_dd[c] = clamped ? 0.0f : P.R * (dr_dh[0] * Jh[0][c] + dr_dh[1] * Jh[1][c] + dr_dh[2] * Jh[2][c]);
+    // Eq. 14: angular fractions
+    const float ig = 1.0f / P.gamma;
+    const float afx = ht * ig, afy = hb * ig;
+    G.fx = L.v[1] + L.v[3];          // = fx (v1 + v3 = fx (1 - fy) + fx fy)
+    G.fy = L.v[2] + L.v[3];
+    (void)afx; (void)afy;
+    for (int c = 0; c < 3; ++c) { G.dfx_dd[c] = Jh[0][c] * ig; G.dfy_dd[c] = Jh[1][c] * ig; }
+    // shade = F G D(n) E / (4 R cos_v)
+    const float vh = v[0] * h[0] + v[1] * h[1] + v[2] * h[2];
+    const float om = 1.0f - vh;
+    const float Fr_ = P.F0 + (1.0f - P.F0) * (om * om) * (om * om) * om;
+    const float dF_dvh = -5.0f * (1.0f - P.F0) * (om * om) * (om * om);
+    float dlv_da[2], dlv_dw[3], dll_da[2], dll_dw[3];
+    const float lam_v = lambda_grad(P.ndf, ax, ay, v, dlv_da, dlv_dw);
+    const float lam_l = lambda_grad(P.ndf, ax, ay, ll, dll_da, dll_dw);
+    const float Gs = 1.0f / ((1.0f + lam_v) * (1.0f + lam_l));
+    const float Dn = 1.0f / (3.14159265358979f * ax * ay);
+    float E;
+    if (kl.kind == 0) E = __ldg(F.light_px + (size_t)l * F.npx + px).w; else E = kl.E;
+    const float base = Dn * E / (4.0f * P.R * S.cos_v);
+    for (int c = 0; c < 2; ++c) {
+        const float dG = -Gs * (dlv_da[c] / (1.0f + lam_v) + dll_da[c] / (1.0f + lam_l));
+        const float dDn = -Dn / (c == 0 ? ax : ay);
+        G.ds_da[c] = Fr_ * (dG * Dn + Gs * dDn) * E / (4.0f * P.R * S.cos_v);
+    }
+    for (int c = 0; c < 3; ++c) {
+        const float dvh = v[0] * Jh[0][c] + v[1] * Jh[1][c] + v[2] * Jh[2][c];
+        const float dlam = dll_dw[0] * Jl[0][c] + dll_dw[1] * Jl[1][c] + dll_dw[2] * Jl[2][c];
+        const float dG = -Gs * dlam / (1.0f + lam_l);
+        G.ds_dd[c] = (dF_dvh * dvh * Gs + Fr_ * dG) * base;
+    }
+}
+
+// Relaxed value and gradient of one pixel (g[0..ng), FP64).  Returns the
+// relaxed radiance.
+__device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& F, int px, double* g, int ng) {
+    for (int k = 0; k < ng; ++k) g[k] = 0.0;
+    PixelSetup S;
+    setup_pixel(P, T, F, px, S);
+    if (S.status != 0) return 0.0f;
+    float out = 0.0f;
+    double acc[kMaxGrad];
+    for (int k = 0; k < ng; ++k) acc[k] = 0.0;
+    for (int l = 0; l < F.nL; ++l) {
+        LightState L;
+        setup_light(P, F, S, px, l, L);
+        if (!L.on) continue;
+        LightGrad LG;
+        light_grad(P, F, S, px, l, L, LG);
+        CountLaw law[4];
+        for (int i = 0; i < 4; ++i) law[i] = count_law(S.ntr[i], L.p);
+        float C = 0.0f, Su = 0.0f, Svx = 0.0f, Svy = 0.0f;
+        float Z0[4] = {0, 0, 0, 0}, Z1[4] = {0, 0, 0, 0};
+        for (int sub = 0; sub < S.K; ++sub) {
+            SubState U;
+            if (!setup_sub(P, T, S, sub, U)) {
+                for (int k = 0; k < ng; ++k) g[k] = 0.0;
+                return 0.0f;
+            }
+            for (int i = 0; i < 4; ++i) {
+                float X[3];
+                for (int j = 0; j < 3; ++j) {
+                    float ct[4];
+                    float z0 = 0.0f, z1 = 0.0f;
+                    for (int k = 0; k < 4; ++k) {
+                        ct[k] = 0.0f;
+                        const uint32_t h0 = fmix32(U.S0[3 * i + j] + L.A0[k]);
+                        if (gate_open(h0, law[i].Tg)) {
+                            const float z = normal_of_word(fmix32(U.S1[3 * i + j] + L.A1[k]));
+                            const float cc = 1.0f + law[i].mu + law[i].sig * z;
+                            ct[k] = fminf(fmaxf(cc, 1.0f), law[i].nceil);
+                            if (cc > 1.0f && cc < law[i].nceil) { z0 += L.v[k]; z1 += L.v[k] * z; }
+                        }
+                    }
+                    X[j] = L.v[0] * ct[0] + L.v[1] * ct[1] + L.v[2] * ct[2] + L.v[3] * ct[3];
+                    const float u = U.uw[3 * i + j];
+                    C += u * X[j];
+                    Svx += u * ((1.0f - LG.fy) * (ct[1] - ct[0]) + LG.fy * (ct[3] - ct[2]));
+                    Svy += u * ((1.0f - LG.fx) * (ct[2] - ct[0]) + LG.fx * (ct[3] - ct[1]));
+                    Z0[i] += u * z0;
+                    Z1[i] += u * z1;
+                }
+                const float hx = 0.5f * U.qx[i], hy = 0.5f * U.qy[i];
+                Su += U.lower[i] ? hx * (X[1] - X[0]) + hy * (X[2] - X[1]) : hy * (X[1] - X[0]) + hx * (X[2] - X[1]);
+            }
+        }
+        // d C / d theta through the count parameters of each tetrahedron vertex
+        double dC[kMaxGrad];
+        for (int k = 0; k < ng; ++k) dC[k] = 0.0;
+        const float p = L.p;
+        for (int i = 0; i < 4; ++i) {
+            const float n = S.ntr[i];
+            const float nm1 = n > 1.0f ? n - 1.0f : 0.0f;
+            const float dnm1 = n > 1.0f ? S.dntr[i] : 0.0f;
+            const float mu = law[i].mu, sig = law[i].sig;
+            // d mu = nm1 dp + p dnm1;  d sigma = ((1 - p) d mu - mu dp) / (2 sigma)
+            auto add = [&](int k, float dp, float dn) {
+                const float dmu = nm1 * dp + p * dn;
+                const float dsig = sig > 0.0f ? ((1.0f - p) * dmu - mu * dp) / (2.0f * sig) : 0.0f;
+                dC[k] += (double)dmu * Z0[i] + (double)dsig * Z1[i];
+            };
+            add(0, LG.dp_da[0], 0.0f);
+            add(1, LG.dp_da[1], 0.0f);
+            add(2, 0.0f, dnm1);
+            if (LG.dir)
+                for (int c = 0; c < 3; ++c) add(3 + 3 * l + c, LG.dp_dd[c], 0.0f);
+        }
+        dC[2] += Su;
+        if (LG.dir)
+            for (int c = 0; c < 3; ++c) dC[3 + 3 * l + c] += (double)Svx * LG.dfx_dd[c] + (double)Svy * LG.dfy_dd[c];
+        // out_l = shade C / A;  d A / d ln rho = A
+        const double iA = 1.0 / (double)S.A.hi;
+        const double outl = (double)L.shade * C * iA;
+        out += (float)outl;
+        acc[0] += ((double)LG.ds_da[0] * C + (double)L.shade * dC[0]) * iA;
+        acc[1] += ((double)LG.ds_da[1] * C + (double)L.shade * dC[1]) * iA;
+        acc[2] += (double)L.shade * dC[2] * iA - outl;
+        if (LG.dir)
+            for (int c = 0; c < 3; ++c)
+                acc[3 + 3 * l + c] += ((double)LG.ds_dd[c] * C + (double)L.shade * dC[3 + 3 * l + c]) * iA;
+    }
+    for (int k = 0; k < ng; ++k) g[k] = acc[k];
+    return out;
+}
+
+__global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant__ KParams P, const FrameDesc F,
+                                                          const float* grad_out, float* out_relaxed,
+                                                          double* partial, int ng) {
+    __shared__ Tables T;
+    __shared__ double red[kBwdThreads];
+    const int nwords = (int)(sizeof(DfTables) / 4) + rot_entries(P.M) * (int)(sizeof(RotEntry) / 4);
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&P.tables);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&T);
+        for (int k = threadIdx.x; k < nwords; k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    double mine[kMaxGrad];
+    for (int k = 0; k < ng; ++k) mine[k] = 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int px = blockIdx.x * blockDim.x + threadIdx.x; px < F.npx; px += stride) {
+        double g[kMaxGrad];
+        const float o = pixel_grad(P, T, F, px, g, ng);
+        if (out_relaxed) out_relaxed[px] = o;
+        const double go = (double)grad_out[px];
+        if (go != 0.0)
+            for (int k = 0; k < ng; ++k) mine[k] += go * g[k];
+    }
+    // fixed-order tree reduction of each component over the CTA
+    for (int k = 0; k < ng; ++k) {
+        red[threadIdx.x] = mine[k];
+        __syncthreads();
+        for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ng + k] = red[0];
+        __syncthreads();
+    }
+}
+
+// grad[k] = sum over CTA partials, in CTA order.
+__global__ void bwd_reduce_kernel(const double* partial, int nblocks, int ng, float* grad) {
+    const int k = threadIdx.x;
+    if (k >= ng) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * ng + k];
+    grad[k] = (float)s;
+}
+
+int bwd_blocks(int npx) {
+    const int sms = num_sms() > 0 ? num_sms() : 1;
+    const int need = (npx + kBwdThreads - 1) / kBwdThreads;
+    const int cap = sms * 4;
+    return need < cap ? need : cap;
+}
+
+}  // namespace glint
+
+using namespace glint;
+
+extern "C" {
+
+size_t glint_backward_workspace_size(const GlintFrame* frame) {
+    if (!frame || frame->width <= 0 || frame->height <= 0 || frame->n_lights < 0 || frame->n_lights > GLINT_MAX_LIGHTS)
+        return 0;
+    const int ng = 3 + 3 * frame->n_lights;
+    return (size_t)bwd_blocks(frame->width * frame->height) * ng * sizeof(double);
+}
+
+int glint_backward(const GlintFrame* frame, const GlintMaterial* material, const GlintLight* lights,
+                   const float* grad_out, float* grad, float* out_relaxed, void* workspace, size_t ws_bytes,
+                   void* stream) {
+    int rc = check_frame_shape(frame, lights);
+    if (rc) return rc;
+    if (frame->mat_px) return GLINT_ERR_UNSUPPORTED;            // gradients of the scalar material only
+    KParams P;
+    if ((rc = make_material_params(material, lights, frame->n_lights, &P))) return rc;
+    if ((rc = check_frame_device(frame, lights))) return rc;
+    if ((rc = check_device_ptr(grad_out, 4)) || (rc = check_device_ptr(grad, 4))) return rc;
+    if (out_relaxed && (rc = check_device_ptr(out_relaxed, 4))) return rc;
+    const size_t need = glint_backward_workspace_size(frame);
+    if (!workspace || ws_bytes < need) return GLINT_ERR_WORKSPACE;
+    if ((rc = check_device_ptr(workspace, 8))) return rc;
+    const FrameDesc F = make_frame_desc(frame, nullptr);
+    const int ng = 3 + 3 * frame->n_lights;
+    const int blocks = bwd_blocks(F.npx);
+    cudaStream_t s = (cudaStream_t)stream;
+    bwd_kernel<<<blocks, kBwdThreads, 0, s>>>(P, F, grad_out, out_relaxed, static_cast<double*>(workspace), ng);
+    if ((rc = cuda_rc(cudaGetLastError()))) return rc;
+    bwd_reduce_kernel<<<1, 32, 0, s>>>(static_cast<const double*>(workspace), blocks, ng, grad);
+    return cuda_rc(cudaGetLastError());
+}
+
+}  // extern "C"

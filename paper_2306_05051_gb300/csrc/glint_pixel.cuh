@@ -167,6 +167,7 @@ struct PixelSetup {
     df sig0, sig1, u0x, u0y;
     Vert vert[4];
     float ntr[4];       // trials of the 4 tetrahedron vertices (per sub-footprint)
+    float dntr[4];      // d ntr / d ln(density) (adjoint)
     df srho;
     // shading frame and view direction (local frame), for the lights
     df n[3], tg[3], b[3], wv[3];
@@ -358,12 +359,18 @@ static __device__ __noinline__ void setup_pixel(const KParams& P, const Tables& 
         vtri[2] = 1; vup[2] = 1; w[2] = lam[1];
         vtri[3] = 2; vup[3] = 1; w[3] = s - C2;
     }
+    // d s / d ln(density) = A_s / (f^l (f - 1)); the first tetrahedron vertex
+    // loses and the last gains weight with s (every tetrahedron), the middle
+    // two do not depend on s.  Pinned: n_i = w_i A_s.
+    const float ds = pinned ? 0.0f : scale2(As, -level * P.log2f).hi / (float)(P.f - 1);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         S.vert[i] = tv[vtri[i]];
         S.vert[i].level = level + vup[i];
         const df ni = pinned ? w[i] * As : scale2(w[i], S.vert[i].level * P.log2f);
         S.ntr[i] = ni.hi;
+        const float dw = i == 0 ? -ds : (i == 3 ? ds : 0.0f);
+        S.dntr[i] = pinned ? ni.hi : dw * pow2f((S.vert[i].level) * P.log2f);
     }
     S.status = 0;
 }
@@ -448,6 +455,8 @@ struct SubState {
     float uw[12];                 // barycentric weights
     int32_t li[12], lj[12];       // lattice vertices (traces)
     uint32_t gid[4];
+    float qx[4], qy[4];           // lattice coordinates (adjoint: d q / d ln(density) = q / 2)
+    bool lower[4];                // simplex half: fx >= fy
 };
 
 // returns false when a lattice coordinate leaves |q| < 2^30
@@ -480,6 +489,7 @@ static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T,
         // barycentric weights, each rounded once from double-float fractions
         // (full relative precision)
         const bool lower = !dflt(fxd, fyd);
+        U.qx[i] = qx.hi; U.qy[i] = qy.hi; U.lower[i] = lower;
         const df hi = lower ? fxd : fyd, lo = lower ? fyd : fxd;     // larger / smaller fraction
         const df dd = hi - lo;
         U.li[3 * i + 0] = i0; U.lj[3 * i + 0] = j0;

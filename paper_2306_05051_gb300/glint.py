@@ -178,3 +178,58 @@ class BatchContext:
             rc = _lib.lib().glint_eval_batch(self._h, frames, n, C.byref(mat), lts, optr, _stream_handle(stream))
         _lib.check(rc, "glint_eval_batch")
         return outs
+
+
+def backward(scene: Scene, grad_out: torch.Tensor, material=None, lights=None, relaxed=False, stream=None):
+    """glint_backward: gradient of sum(grad_out * relaxed image) with respect
+    to (alpha_x, alpha_y, ln_density, light directions).  Returns the
+    gradient (3 + 3 * n_lights floats, device) and the relaxed image when
+    requested."""
+    material = material or scene.material
+    lights = scene.lights if lights is None else lights
+    dev = scene.gbuf.device
+    H, W = scene.height, scene.width
+    _check_plane(grad_out, "grad_out", (H, W), dev)
+    frame = _lib.frame_struct(scene.gbuf, scene.light_px, scene.mat_px, len(lights))
+    nbytes = int(_lib.lib().glint_backward_workspace_size(C.byref(frame)))
+    ws = torch.empty(max(nbytes, 8) // 8 + 1, dtype=torch.float64, device=dev)
+    grad = torch.empty(3 + 3 * len(lights), dtype=torch.float32, device=dev)
+    rel = torch.empty(H, W, dtype=torch.float32, device=dev) if relaxed else None
+    mat = _lib.material_struct(material)
+    lts = _lib.lights_struct(lights)
+    with torch.cuda.device(dev):
+        rc = _lib.lib().glint_backward(C.byref(frame), C.byref(mat), lts, grad_out.data_ptr(), grad.data_ptr(),
+                                       None if rel is None else rel.data_ptr(), ws.data_ptr(),
+                                       ws.numel() * 8, _stream_handle(stream))
+    _lib.check(rc, "glint_backward")
+    return (grad, rel) if relaxed else grad
+
+
+class GlintBRDF(torch.autograd.Function):
+    """Glint image as a differentiable function of the scalar material
+    roughness, ln flake density and the directions of directional lights.
+    Forward: the glint image (integer counts).  Backward: the gradient of the
+    relaxed image (counts before integer rounding), discrete choices fixed.
+
+        img = GlintBRDF.apply(alpha_x, alpha_y, ln_density, light_dirs, scene)
+    alpha_x, alpha_y, ln_density: 0-d tensors; light_dirs: [n_lights, 3]."""
+
+    @staticmethod
+    def forward(ctx, alpha_x, alpha_y, ln_density, light_dirs, scene):
+        import dataclasses
+        mat = dataclasses.replace(scene.material, alpha_x=float(alpha_x), alpha_y=float(alpha_y),
+                                  ln_density=float(ln_density))
+        dirs = light_dirs.detach().cpu().tolist()
+        lights = [dataclasses.replace(L, dir=tuple(dirs[k])) if L.kind == 1 else L
+                  for k, L in enumerate(scene.lights)]
+        ctx.scene, ctx.mat, ctx.lights = scene, mat, lights
+        ctx.dev_dtype = (alpha_x.device, alpha_x.dtype, light_dirs.device, light_dirs.dtype)
+        return render_scene(scene, material=mat, lights=lights)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = backward(ctx.scene, grad_out.contiguous().float(), material=ctx.mat, lights=ctx.lights)
+        adev, adt, ddev, ddt = ctx.dev_dtype
+        ga = g[:3].to(device=adev, dtype=adt)
+        gd = g[3:].reshape(-1, 3).to(device=ddev, dtype=ddt)
+        return ga[0], ga[1], ga[2], gd, None
