@@ -225,6 +225,50 @@ def run_batched(args, dev):
             "plain_launches_per_batch": len(frames)}
 
 
+def run_fwd_bwd(args, dev):
+    """512^2 plane + sphere fit scene: glint_eval then glint_backward of an
+    L2 loss against the perturbed-parameter target image, per step."""
+    from paper_2306_05051_gb300 import glint, scenes
+    sc = scenes.plane_sphere_fit(device=dev)
+    tgt = scenes.plane_sphere_fit(target=True)
+    stream = torch.cuda.Stream(device=dev)
+    img = torch.empty(sc.height, sc.width, dtype=torch.float32, device=dev)
+    timg = glint.render_scene(sc, material=tgt.material, lights=tgt.lights)
+    ws = torch.empty(glint.backward_workspace_bytes(sc) // 8 + 1, dtype=torch.float64, device=dev)
+    grad = torch.empty(6, dtype=torch.float32, device=dev)
+    go = torch.empty_like(img)
+    torch.cuda.synchronize(dev)
+
+    def step():
+        glint.render_scene(sc, out=img, stream=stream)
+        with torch.cuda.stream(stream):
+            torch.sub(img, timg, out=go)
+            go.mul_(2.0)
+        glint.backward(sc, go, stream=stream, workspace=ws, grad=grad)
+
+    for _ in range(args.warmup):
+        step()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    steps = max(3, min(args.steps, 20))
+    stream.synchronize()
+    ev[0].record(stream)
+    for _ in range(steps):
+        step()
+    ev[1].record(stream)
+    ev[1].synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / steps
+    ev[0].record(stream)
+    for _ in range(steps):
+        glint.backward(sc, go, stream=stream, workspace=ws, grad=grad)
+    ev[1].record(stream)
+    ev[1].synchronize()
+    ms_b = ev[0].elapsed_time(ev[1]) / steps
+    return {"workload": "plane_sphere_fit 512x512, directional light, L2 loss vs perturbed-parameter target, "
+                        "gradients w.r.t. alpha_x, alpha_y, ln density, light direction",
+            "ms_per_step": ms, "backward_ms": ms_b, "gpu_launches_per_step": 3,
+            "grad": [float(x) for x in grad.cpu()]}
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle on the host cores on a deterministic row sample of the
     same 4K frame (every 64th row, then further rows until ~seconds)."""
@@ -256,6 +300,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-fwd-bwd", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -319,6 +364,8 @@ def main():
     }
     if not args.no_batched:
         line["batched"] = run_batched(args, dev)
+    if not args.no_fwd_bwd:
+        line["fwd_bwd"] = run_fwd_bwd(args, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -180,11 +180,19 @@ class BatchContext:
         return outs
 
 
-def backward(scene: Scene, grad_out: torch.Tensor, material=None, lights=None, relaxed=False, stream=None):
+def backward_workspace_bytes(scene: Scene, lights=None) -> int:
+    lights = scene.lights if lights is None else lights
+    frame = _lib.frame_struct(scene.gbuf, scene.light_px, scene.mat_px, len(lights))
+    return int(_lib.lib().glint_backward_workspace_size(C.byref(frame)))
+
+
+def backward(scene: Scene, grad_out: torch.Tensor, material=None, lights=None, relaxed=False, stream=None,
+             workspace=None, grad=None, out_relaxed=None):
     """glint_backward: gradient of sum(grad_out * relaxed image) with respect
     to (alpha_x, alpha_y, ln_density, light directions).  Returns the
     gradient (3 + 3 * n_lights floats, device) and the relaxed image when
-    requested."""
+    requested.  workspace (float64 device tensor), grad and out_relaxed may be
+    passed in to avoid allocations."""
     material = material or scene.material
     lights = scene.lights if lights is None else lights
     dev = scene.gbuf.device
@@ -192,9 +200,11 @@ def backward(scene: Scene, grad_out: torch.Tensor, material=None, lights=None, r
     _check_plane(grad_out, "grad_out", (H, W), dev)
     frame = _lib.frame_struct(scene.gbuf, scene.light_px, scene.mat_px, len(lights))
     nbytes = int(_lib.lib().glint_backward_workspace_size(C.byref(frame)))
-    ws = torch.empty(max(nbytes, 8) // 8 + 1, dtype=torch.float64, device=dev)
-    grad = torch.empty(3 + 3 * len(lights), dtype=torch.float32, device=dev)
-    rel = torch.empty(H, W, dtype=torch.float32, device=dev) if relaxed else None
+    ws = workspace if workspace is not None else torch.empty(max(nbytes, 8) // 8 + 1, dtype=torch.float64, device=dev)
+    if grad is None:
+        grad = torch.empty(3 + 3 * len(lights), dtype=torch.float32, device=dev)
+    rel = out_relaxed if out_relaxed is not None else (
+        torch.empty(H, W, dtype=torch.float32, device=dev) if relaxed else None)
     mat = _lib.material_struct(material)
     lts = _lib.lights_struct(lights)
     with torch.cuda.device(dev):
@@ -202,7 +212,7 @@ def backward(scene: Scene, grad_out: torch.Tensor, material=None, lights=None, r
                                        None if rel is None else rel.data_ptr(), ws.data_ptr(),
                                        ws.numel() * 8, _stream_handle(stream))
     _lib.check(rc, "glint_backward")
-    return (grad, rel) if relaxed else grad
+    return (grad, rel) if (relaxed or out_relaxed is not None) else grad
 
 
 class GlintBRDF(torch.autograd.Function):
