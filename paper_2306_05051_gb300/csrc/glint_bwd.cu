@@ -151,17 +151,17 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
     for (int k = 0; k < ng; ++k) acc[k] = 0.0;
     for (int l = 0; l < F.nL; ++l) {
         LightState L;
-        setup_light(P, F, S, px, l, L);
+        setup_light<true>(P, F, S, px, l, L);
         if (!L.on) continue;
         LightGrad LG;
         light_grad(P, F, S, px, l, L, LG);
         CountLaw law[4];
-        for (int i = 0; i < 4; ++i) law[i] = count_law(S.ntr[i], L.p);
+        for (int i = 0; i < 4; ++i) law[i] = count_law(S.ntr[i], L.p, L.lq);
         float C = 0.0f, Su = 0.0f, Svx = 0.0f, Svy = 0.0f;
         float Z0[4] = {0, 0, 0, 0}, Z1[4] = {0, 0, 0, 0};
         for (int sub = 0; sub < S.K; ++sub) {
             SubState U;
-            if (!setup_sub(P, T, S, sub, U)) {
+            if (!setup_sub<true>(P, T, S, sub, U, U.S0, U.uw, 1)) {
                 for (int k = 0; k < ng; ++k) g[k] = 0.0;
                 return 0.0f;
             }

@@ -14,7 +14,6 @@
 
 namespace glint {
 
-constexpr int kWarpsPerBlock = 8;
 constexpr int kQ = 64;                    // queue capacity per warp (ring)
 
 struct WarpQueue {
@@ -64,14 +63,15 @@ __device__ __noinline__ void flush_queue(WarpQueue& q, int head, int n, float& a
 
 struct LightEval {          // what the evaluation loop needs of one light
     bool on;
-    float p, shade;
+    float p, lq, shade;
     float v[4];
     uint32_t A0[4], A1[4];
 };
 
 // Shade the pixel of this lane (px valid or not); all 32 lanes call together.
+// ss0 / suw: the CTA's shared arrays of 12 x blockDim spatial words / weights.
 __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& F, WarpQueue& q, int px,
-                            bool valid) {
+                            bool valid, uint32_t* ss0, float* suw) {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     PixelSetup S;
@@ -81,39 +81,48 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
     LightState ls[kMaxLights];
     for (int l = 0; l < F.nL; ++l) {
         ls[l].on = false;
-        if (S.status == 0) setup_light(P, F, S, px, l, ls[l]);
+        if (S.status == 0) setup_light<false>(P, F, S, px, l, ls[l]);
     }
     const int K = S.status == 0 ? S.K : 0;
     const int Kw = __reduce_max_sync(0xffffffffu, K);
     float acc = 0.0f;
     int head = 0, count = 0;                     // warp-uniform queue state
     bool in_range = true;
+    // this lane's 12 spatial words and weights, structure-of-arrays in shared memory
+    uint32_t* s0s = ss0 + threadIdx.x;
+    float* uws = suw + threadIdx.x;
+    const int st = blockDim.x;
     for (int sub = 0; sub < Kw; ++sub) {
         SubState U;
         bool act = sub < K && in_range;
         if (act) {
-            in_range = setup_sub(P, T, S, sub, U);
+            in_range = setup_sub<false>(P, T, S, sub, U, s0s, uws, st);
             act = in_range;
         }
 #pragma unroll 1
         for (int l = 0; l < F.nL; ++l) {
             LightEval L;
             L.on = act && ls[l].on;
-            L.p = ls[l].p; L.shade = ls[l].shade;
+            L.p = ls[l].p; L.lq = ls[l].lq; L.shade = ls[l].shade;
 #pragma unroll
             for (int k = 0; k < 4; ++k) { L.v[k] = ls[l].v[k]; L.A0[k] = ls[l].A0[k]; L.A1[k] = ls[l].A1[k]; }
             if (!__any_sync(0xffffffffu, L.on)) continue;
 #pragma unroll 1
             for (int i = 0; i < 4; ++i) {
-                CountLaw law = count_law(S.ntr[i], L.p);
+                CountLaw law = count_law(S.ntr[i], L.p, L.lq);
                 if (!L.on) law.Tg = 0u;
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    const uint32_t s0 = U.S0[3 * i + j], s1 = U.S1[3 * i + j];
-                    const float uw = U.uw[3 * i + j] * L.shade;
+                    const uint32_t s0 = s0s[(3 * i + j) * st], s1 = U.S1[3 * i + j];
+                    const float uw = uws[(3 * i + j) * st] * L.shade;
+                    // one warp vote for the 4 angular texels: most groups have no open gate
+                    bool gk[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) gk[k] = gate_open(fmix32(s0 + L.A0[k]), law.Tg);
+                    if (!__any_sync(0xffffffffu, gk[0] | gk[1] | gk[2] | gk[3])) continue;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const bool g = gate_open(fmix32(s0 + L.A0[k]), law.Tg);
+                        const bool g = gk[k];
                         const unsigned m = __ballot_sync(0xffffffffu, g);
                         if (m) {
                             if (g) {
@@ -148,6 +157,8 @@ __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KPara
     extern __shared__ __align__(16) unsigned char smem[];
     Tables& T = *reinterpret_cast<Tables*>(smem);
     WarpQueue* Qs = reinterpret_cast<WarpQueue*>(smem + sizeof(Tables));
+    uint32_t* ss0 = reinterpret_cast<uint32_t*>(Qs + blockDim.x / 32);
+    float* suw = reinterpret_cast<float*>(ss0 + 12 * blockDim.x);
     load_tables(P, T);
     WarpQueue& q = Qs[threadIdx.x >> 5];
     // Block-uniform tiles of blockDim.x pixels.  The barrier at the top of a
@@ -156,7 +167,7 @@ __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KPara
     for (int base = blockIdx.x * blockDim.x; base < F.npx; base += gridDim.x * blockDim.x) {
         __syncthreads();
         const int px = base + (int)threadIdx.x;
-        const float o = shade_warp(P, T, F, q, px, px < F.npx);
+        const float o = shade_warp(P, T, F, q, px, px < F.npx, ss0, suw);
         if (px < F.npx) F.out[px] = o;
     }
 }
@@ -169,6 +180,8 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KPa
     extern __shared__ __align__(16) unsigned char smem[];
     Tables& T = *reinterpret_cast<Tables*>(smem);
     WarpQueue* Qs = reinterpret_cast<WarpQueue*>(smem + sizeof(Tables));
+    uint32_t* ss0 = reinterpret_cast<uint32_t*>(Qs + blockDim.x / 32);
+    float* suw = reinterpret_cast<float*>(ss0 + 12 * blockDim.x);
     __shared__ int tile_s;
     load_tables(P, T);
     WarpQueue& q = Qs[threadIdx.x >> 5];
@@ -185,12 +198,14 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KPa
         }
         const FrameDesc& F = B.frames[lo];
         const int px = (t - B.tile_base[lo]) * (int)blockDim.x + (int)threadIdx.x;
-        const float o = shade_warp(P, T, F, q, px, px < F.npx);
+        const float o = shade_warp(P, T, F, q, px, px < F.npx, ss0, suw);
         if (px < F.npx) F.out[px] = o;
     }
 }
 
-size_t fwd_smem_bytes(int threads) { return sizeof(Tables) + (size_t)(threads / 32) * sizeof(WarpQueue); }
+size_t fwd_smem_bytes(int threads) {
+    return sizeof(Tables) + (size_t)(threads / 32) * sizeof(WarpQueue) + (size_t)threads * 24 * sizeof(uint32_t);
+}
 
 // --------------------------------------------------------------------------
 // parity trace: one thread per listed pixel, every evaluation recorded
@@ -204,18 +219,18 @@ __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& 
     pr->phi = S.status == 0 ? S.phi.hi : 0.0f; pr->out = 0.0f;
     if (S.status != 0) return;
     LightState ls[kMaxLights];
-    for (int l = 0; l < F.nL; ++l) setup_light(P, F, S, px, l, ls[l]);
+    for (int l = 0; l < F.nL; ++l) setup_light<true>(P, F, S, px, l, ls[l]);
     float C[kMaxLights];
     for (int l = 0; l < F.nL; ++l) C[l] = 0.0f;
     int nrec = 0;
     for (int sub = 0; sub < S.K; ++sub) {
         SubState U;
-        if (!setup_sub(P, T, S, sub, U)) { pr->status = 3; pr->n_rec = nrec; return; }
+        if (!setup_sub<true>(P, T, S, sub, U, U.S0, U.uw, 1)) { pr->status = 3; pr->n_rec = nrec; return; }
         for (int l = 0; l < F.nL; ++l) {
             const LightState& L = ls[l];
             if (!L.on) continue;
             for (int i = 0; i < 4; ++i) {
-                const CountLaw law = count_law(S.ntr[i], L.p);
+                const CountLaw law = count_law(S.ntr[i], L.p, L.lq);
                 for (int j = 0; j < 3; ++j) {
                     for (int k = 0; k < 4; ++k) {
                         const uint32_t h0 = fmix32(U.S0[3 * i + j] + L.A0[k]);

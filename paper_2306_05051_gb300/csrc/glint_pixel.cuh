@@ -118,10 +118,11 @@ struct CountLaw {
     float P1, mu, sig, nceil;
 };
 
-__device__ __forceinline__ CountLaw count_law(float n, float p) {
+// lq = log1pf(-p), computed once per pixel and light (setup_light)
+__device__ __forceinline__ CountLaw count_law(float n, float p, float lq) {
     CountLaw c;
     c.P1 = 0.0f;
-    if (n > 0.0f && p > 0.0f) c.P1 = p >= 1.0f ? 1.0f : -expm1f(n * log1pf(-p));
+    if (n > 0.0f && p > 0.0f) c.P1 = p >= 1.0f ? 1.0f : -expm1f(n * lq);
     c.Tg = (uint32_t)ceilf(c.P1 * 33554432.0f);            // 2^25
     const float nm1 = n > 1.0f ? n - 1.0f : 0.0f;
     c.mu = nm1 * p;
@@ -381,13 +382,17 @@ static __device__ __noinline__ void setup_pixel(const KParams& P, const Tables& 
 struct LightState {
     bool on;
     float p, shade;               // p of Eq. 4; F G D(n) E / (4 R cos_v)
+    float lq;                     // log(1 - p) (count laws)
     float v[4];                   // angular bilinear weights
     uint32_t A0[4], A1[4];        // angular hash words
     int32_t ax[4], ay[4];         // angular texels (traces)
 };
 
-static __device__ __noinline__ void setup_light(const KParams& P, const FrameDesc& F, const PixelSetup& S, int px, int l,
-                                               LightState& L) {
+// kTrace: also record the angular texels (ax, ay) for the trace and adjoint
+// kernels; the image kernels skip those stores.
+template <bool kTrace>
+static __device__ __noinline__ void setup_light(const KParams& P, const FrameDesc& F, const PixelSetup& S, int px,
+                                               int l, LightState& L) {
     L.on = false;
     const KLight kl = P.lights[l];
     float lr[3], E;
@@ -420,6 +425,7 @@ static __device__ __noinline__ void setup_light(const KParams& P, const FrameDes
     const float hn2 = hn * hn;
     const float rat = P.ndf == 0 ? expf(-e / hn2) / (hn2 * hn2) : 1.0f / ((e + hn2) * (e + hn2));
     L.p = fminf(P.R * rat, 1.0f);
+    L.lq = log1pf(-L.p);
     // Eq. 14: bilinear angular texels of the projected half-vector; the
     // weights are formed from double-float fractions so each keeps full
     // relative precision however small it is.
@@ -431,8 +437,8 @@ static __device__ __noinline__ void setup_light(const KParams& P, const FrameDes
     L.v[2] = gx * fy; L.v[3] = fx * fy;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        L.ax[k] = ix + (k & 1); L.ay[k] = iy + (k >> 1);
-        uint32_t hx = (uint32_t)L.ax[k], hy = (uint32_t)L.ay[k], hz = ~P.seed;
+        if (kTrace) { L.ax[k] = ix + (k & 1); L.ay[k] = iy + (k >> 1); }
+        uint32_t hx = (uint32_t)(ix + (k & 1)), hy = (uint32_t)(iy + (k >> 1)), hz = ~P.seed;
         pcg3d(hx, hy, hz);
         L.A0[k] = hx; L.A1[k] = hy;
     }
@@ -459,8 +465,14 @@ struct SubState {
     bool lower[4];                // simplex half: fx >= fy
 };
 
-// returns false when a lattice coordinate leaves |q| < 2^30
-static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T, const PixelSetup& S, int sub, SubState& U) {
+// Returns false when a lattice coordinate leaves |q| < 2^30.  The spatial
+// words S0 and weights of texel t go to s0[t * stride], uw[t * stride] (the
+// image kernels keep those two in shared memory; pass U.S0, U.uw and stride 1
+// to keep them in U).  kTrace: also record the lattice vertices and
+// coordinates (li, lj, qx, qy, lower) for the trace and adjoint kernels.
+template <bool kTrace>
+static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T, const PixelSetup& S, int sub,
+                                              SubState& U, uint32_t* s0, float* uwo, int stride) {
     df us = S.u, vs = S.v;
     if (S.K > 1) {
         // centre of sub-rectangle (ia, ib) of the sigma0 x sigma1 rectangle
@@ -489,20 +501,21 @@ static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T,
         // barycentric weights, each rounded once from double-float fractions
         // (full relative precision)
         const bool lower = !dflt(fxd, fyd);
-        U.qx[i] = qx.hi; U.qy[i] = qy.hi; U.lower[i] = lower;
+        if (kTrace) { U.qx[i] = qx.hi; U.qy[i] = qy.hi; U.lower[i] = lower; }
         const df hi = lower ? fxd : fyd, lo = lower ? fyd : fxd;     // larger / smaller fraction
         const df dd = hi - lo;
-        U.li[3 * i + 0] = i0; U.lj[3 * i + 0] = j0;
-        U.uw[3 * i + 0] = __fsub_rn(__fsub_rn(1.0f, hi.hi), hi.lo);
-        U.li[3 * i + 1] = lower ? i0 + 1 : i0; U.lj[3 * i + 1] = lower ? j0 : j0 + 1;
-        U.uw[3 * i + 1] = __fadd_rn(dd.hi, dd.lo);
-        U.li[3 * i + 2] = i0 + 1; U.lj[3 * i + 2] = j0 + 1;
-        U.uw[3 * i + 2] = __fadd_rn(lo.hi, lo.lo);
+        const float w3[3] = {__fsub_rn(__fsub_rn(1.0f, hi.hi), hi.lo), __fadd_rn(dd.hi, dd.lo),
+                             __fadd_rn(lo.hi, lo.lo)};
+        const int li3[3] = {i0, lower ? i0 + 1 : i0, i0 + 1};
+        const int lj3[3] = {j0, lower ? j0 : j0 + 1, j0 + 1};
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            uint32_t hx = (uint32_t)U.li[3 * i + j], hy = (uint32_t)U.lj[3 * i + j], hz = U.gid[i], hw = P.seed;
+            if (kTrace) { U.li[3 * i + j] = li3[j]; U.lj[3 * i + j] = lj3[j]; }
+            uint32_t hx = (uint32_t)li3[j], hy = (uint32_t)lj3[j], hz = U.gid[i], hw = P.seed;
             pcg4d(hx, hy, hz, hw);
-            U.S0[3 * i + j] = hx; U.S1[3 * i + j] = hy;
+            s0[(3 * i + j) * stride] = hx;
+            uwo[(3 * i + j) * stride] = w3[j];
+            U.S1[3 * i + j] = hy;
         }
     }
     return true;
