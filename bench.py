@@ -14,6 +14,7 @@ the host cores on a row sample of the same frame.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -43,6 +44,38 @@ SMS = 152
 LANES_PER_SM = 128
 
 
+PROFILE = os.path.join(ROOT, "profiles", "fwd_kernel_sphere_plane_4k.md")
+
+
+def kernel_source_hash():
+    """sha256 (first 16 hex digits) of the CUDA sources and the C header: a
+    DRAM-traffic figure taken from an ncu capture applies only while this is
+    unchanged."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2306_05051_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)) + ["../../include/glint.h"]:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) per fwd_kernel launch from the committed ncu
+    summary, or None if it was captured on other kernel sources."""
+    try:
+        with open(PROFILE) as fh:
+            kv = dict(l.strip().strip("-* `").split(":", 1) for l in fh if l.strip().strip("-* `").startswith(
+                ("source_hash:", "dram_bytes_per_launch:")))
+    except (OSError, ValueError):
+        return None
+    if kv.get("source_hash", "").strip(" `") != kernel_source_hash():
+        return None
+    try:
+        return int(kv["dram_bytes_per_launch"].strip(" `"))
+    except (KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -64,7 +97,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -295,7 +328,7 @@ def cpu_baseline(seconds=12.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -352,7 +385,8 @@ def main():
                    f"({r['bytes'] / 1e6:.0f} MB read+written per step vs 129 MB L2)",
                    "parallelism": f"replicas x{world} (one frame per GPU)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "T lane-op/s",
-                     "frac": achieved / peak_ops, "traffic": None,
+                     "frac": achieved / peak_ops, "traffic": profiled_traffic(),
+                     "traffic_source": os.path.relpath(PROFILE, ROOT), "kernel_source_hash": kernel_source_hash(),
                      "algorithmic_ops_per_launch": cen["ops"], "evals_per_launch": cen["evals"],
                      "peak_basis": f"{SMS} SMs x {LANES_PER_SM} FP32/INT32 lanes x {mhz:.0f} MHz",
                      "hbm_gbs": r["bytes"] / (r["ms"] * 1e-3) / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs")},

@@ -391,7 +391,7 @@ struct LightState {
 // kTrace: also record the angular texels (ax, ay) for the trace and adjoint
 // kernels; the image kernels skip those stores.
 template <bool kTrace>
-static __device__ __noinline__ void setup_light(const KParams& P, const FrameDesc& F, const PixelSetup& S, int px,
+static __device__ __forceinline__ void setup_light(const KParams& P, const FrameDesc& F, const PixelSetup& S, int px,
                                                int l, LightState& L) {
     L.on = false;
     const KLight kl = P.lights[l];
