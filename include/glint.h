@@ -126,8 +126,11 @@ int glint_eval(const GlintFrame* frame, const GlintMaterial* material,
 
 /* Launch shape of the forward kernel: threads per CTA (128, 256, 512 or
  * 1024; one warp shades 32 consecutive pixels, a CTA a tile of that many
- * pixels) and resident CTAs per SM the grid is sized for (1..16).  The grid
- * is persistent: min(tiles, SMs x ctas_per_sm) CTAs loop over the tiles. */
+ * pixels) and CTAs per SM.  ctas_per_sm = 0 (glint_eval's default, with 512
+ * threads): one CTA per tile, the hardware scheduler balances tiles of
+ * uneven cost over the SMs.  ctas_per_sm = 1..16: a persistent grid of
+ * min(tiles, SMs x ctas_per_sm) CTAs loops over the tiles.  The batched
+ * path (glint_ctx_set_launch) is always persistent and takes 1..16. */
 typedef struct GlintLaunch {
     int32_t threads_per_cta;
     int32_t ctas_per_sm;
@@ -179,7 +182,7 @@ int glint_eval_batch(GlintContext* ctx, const GlintFrame* frames, int32_t n_fram
                      const GlintMaterial* material, const GlintLight* lights,
                      float* const* outs, void* stream);
 
-/* Adjoint (spec differentiation of the counting law, Sec. 3-6):
+/* Adjoint (differentiation of the counting law, Sec. 3-6):
  *   grad[k] = sum_px grad_out[px] * d relaxed(px) / d theta_k,
  * theta = (alpha_x, alpha_y, ln_density, dir of light 0 (xyz), dir of light 1,
  * ...), 3 + 3 * n_lights floats; the direction entries of point lights are 0.

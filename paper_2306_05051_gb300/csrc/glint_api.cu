@@ -104,7 +104,7 @@ namespace {
 std::mutex g_dev_mutex;
 int g_sm_count[64];
 constexpr int kDefaultThreads = 512;
-constexpr int kDefaultCtasPerSm = 2;
+constexpr int kDefaultCtasPerSm = 0;       // one CTA per tile, scheduled by the hardware
 
 }  // namespace
 
@@ -176,9 +176,14 @@ int check_frame_device(const GlintFrame* f, const GlintLight* lights) {
     return GLINT_OK;
 }
 
+// ctas_per_sm == 0: one CTA per tile, so the hardware block scheduler hands
+// tiles to SMs as they free up (tiles differ in cost: sky, lit surface, dense
+// flakes); otherwise a persistent grid of SMs x ctas_per_sm CTAs strides over
+// the tiles.
 FwdLaunch make_fwd_launch(int npx, int threads, int ctas_per_sm) {
-    const int sms = num_sms() > 0 ? num_sms() : 1;
     const int need = (npx + threads - 1) / threads;
+    if (ctas_per_sm == 0) return FwdLaunch{threads, need};
+    const int sms = num_sms() > 0 ? num_sms() : 1;
     const int cap = sms * ctas_per_sm;
     return FwdLaunch{threads, need < cap ? need : cap};
 }
@@ -216,7 +221,7 @@ int glint_eval_launch(const GlintFrame* frame, const GlintMaterial* material, co
                       float* out, const GlintLaunch* launch, void* stream) {
     if (!launch) return GLINT_ERR_ARG;
     const int t = launch->threads_per_cta;
-    if ((t != 128 && t != 256 && t != 512 && t != 1024) || launch->ctas_per_sm < 1 || launch->ctas_per_sm > 16)
+    if ((t != 128 && t != 256 && t != 512 && t != 1024) || launch->ctas_per_sm < 0 || launch->ctas_per_sm > 16)
         return GLINT_ERR_ARG;
     KParams P;
     FrameDesc F;

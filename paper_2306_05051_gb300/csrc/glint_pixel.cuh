@@ -185,7 +185,7 @@ __device__ __forceinline__ bool load_gbuf(const FrameDesc& F, int px, float4& g0
     return finite;
 }
 
-static __device__ __noinline__ void setup_pixel(const KParams& P, const Tables& T, const FrameDesc& F, int px,
+static __device__ __forceinline__ void setup_pixel(const KParams& P, const Tables& T, const FrameDesc& F, int px,
                                                PixelSetup& S) {
     S.status = 2;
     S.K = 0;

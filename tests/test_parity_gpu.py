@@ -173,3 +173,22 @@ def test_invalid_device_arguments():
     with pytest.raises(_lib.GlintError) as e:
         glint.render(g, sc.light_px.to(DEV), None, sc.material, sc.lights)
     assert e.value.code == -2
+
+
+def test_every_launch_shape_gives_the_same_bits():
+    """glint_eval_launch: one CTA per tile (ctas_per_sm = 0) and persistent
+    grids of every CTA size give glint_eval's image bit for bit; bad shapes
+    are rejected."""
+    from paper_2306_05051_gb300 import _lib
+    sc = scenes.sphere_plane(640, 360, seed=5)
+    scd = sc.to(DEV)
+    ref = glint.render_scene(scd)
+    for shape in [(512, 0), (128, 0), (1024, 0), (128, 1), (256, 4), (256, 8), (512, 2), (1024, 1), (1024, 2),
+                  (512, 16)]:
+        img = glint.render_scene(scd, launch=shape)
+        torch.cuda.synchronize()
+        assert torch.equal(img, ref), shape
+    for bad in [(512, -1), (512, 17), (100, 2), (2048, 1)]:
+        with pytest.raises(_lib.GlintError) as e:
+            glint.render_scene(scd, launch=bad)
+        assert e.value.code == -1, bad
