@@ -125,7 +125,7 @@ int glint_eval(const GlintFrame* frame, const GlintMaterial* material,
                const GlintLight* lights, float* out, void* stream);
 
 /* Launch shape of the forward kernel: threads per CTA (128, 256, 512 or
- * 1024; one warp shades 32 consecutive pixels, a CTA a tile of that many
+ * 1024; one warp shades 32 pixels, a CTA a tile of that many consecutive
  * pixels) and CTAs per SM.  ctas_per_sm = 0 (glint_eval's default, with 512
  * threads): one CTA per tile, the hardware scheduler balances tiles of
  * uneven cost over the SMs.  ctas_per_sm = 1..16: a persistent grid of

@@ -1,7 +1,8 @@
 // Plain forward kernel (one frame) and the parity-trace kernel.
 //
-// Forward kernel mapping: one warp shades 32 consecutive pixels (lane =
-// pixel) for the per-pixel, per-light and per-sub-footprint setup, then walks
+// Forward kernel mapping: one warp shades 32 pixels of its CTA's tile (lane =
+// pixel, 8 groups of 4 consecutive pixels, see tile_pixel) for the
+// per-pixel, per-light and per-sub-footprint setup, then walks
 // the evaluations in a warp-uniform loop (sub-footprint, light, 4 grids x 3
 // simplex vertices x 4 angular texels).  Each lane tests its gate with one
 // hash word; the rare open gates (their count needs the second word, a normal
@@ -153,6 +154,17 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
     return acc / S.A.hi;
 }
 
+// Pixel of this thread in a tile of blockDim.x pixels: lanes take groups of 4
+// consecutive pixels spread over the whole tile (warp w, lane l -> group
+// (l / 4) * warps + w).  Neighbouring pixels cost about the same (same lights
+// on, same flake density), so spreading each warp over the tile evens out
+// the warps' work, and the warps wait less at the tile barrier.
+__device__ __forceinline__ int tile_pixel() {
+    const int nw = (int)blockDim.x >> 5;
+    const int ln = (int)threadIdx.x & 31, w = (int)threadIdx.x >> 5;
+    return (ln >> 2) * (nw * 4) + w * 4 + (ln & 3);
+}
+
 __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KParams P, const FrameDesc F) {
     extern __shared__ __align__(16) unsigned char smem[];
     Tables& T = *reinterpret_cast<Tables*>(smem);
@@ -166,7 +178,7 @@ __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KPara
     // straight-line) setup code so they share instruction-cache lines.
     for (int base = blockIdx.x * blockDim.x; base < F.npx; base += gridDim.x * blockDim.x) {
         __syncthreads();
-        const int px = base + (int)threadIdx.x;
+        const int px = base + tile_pixel();
         const float o = shade_warp(P, T, F, q, px, px < F.npx, ss0, suw);
         if (px < F.npx) F.out[px] = o;
     }
@@ -197,7 +209,7 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KPa
             if (B.tile_base[mid] <= t) lo = mid; else hi = mid - 1;
         }
         const FrameDesc& F = B.frames[lo];
-        const int px = (t - B.tile_base[lo]) * (int)blockDim.x + (int)threadIdx.x;
+        const int px = (t - B.tile_base[lo]) * (int)blockDim.x + tile_pixel();
         const float o = shade_warp(P, T, F, q, px, px < F.npx, ss0, suw);
         if (px < F.npx) F.out[px] = o;
     }
