@@ -40,6 +40,7 @@ OPS_PER_SUB = 350          # LOD, cell, tetrahedron, 4 grid transforms + simplex
 OPS_PER_PIXEL_LIGHT = 180  # half-vector, NDF ratio, angular texels + 4 hashes, Fresnel, Smith, shade
 OPS_PER_SUB_LIGHT = 60     # 4 gated-binomial parameter sets (P>=1, mu, sigma, ceil n)
 OPS_PER_EVAL = 11          # one hash word (combine + fmix32) and the gate test
+ADJOINT_FACTOR = 1.5       # adjoint work per forward op (backward = forward recomputed + adjoint)
 SMS = 152
 LANES_PER_SM = 128
 
@@ -215,6 +216,18 @@ def run_ours(args, rank, world, dev):
                 bytes=frame_bytes(scd))
 
 
+def peak_lane_ops():
+    """T lane-op/s: SMs x FP32/INT32 lanes x maximum SM clock."""
+    mhz = float(_peaks().get("sm_max_mhz", 2070.0))
+    return SMS * LANES_PER_SM * mhz * 1e6 / 1e12
+
+
+def roofline_of(ops, ms):
+    a = ops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": a, "peak": peak_lane_ops(), "unit": "T lane-op/s",
+            "frac": a / peak_lane_ops(), "algorithmic_ops": ops}
+
+
 def run_batched(args, dev):
     """64-frame camera orbit of the sphere scene at mixed resolutions (16 each
     of 256^2, 512^2, 1280x720, 1920x1080): one persistent launch replayed
@@ -250,9 +263,12 @@ def run_batched(args, dev):
     ms_p = ev0.elapsed_time(ev1) / steps
     launch = ctx.launch
     ctx.close()
+    ops = sum(census(glint, f)["ops"] for f in frames)
+    nbytes = sum(frame_bytes(f) for f in frames)
     return {"workload": "orbit of the sphere scene, 64 frames (16 each of 256x256, 512x512, 1280x720, "
                         "1920x1080), 2 point lights, per-pixel material",
             "pixels": npx, "value": npx / (ms_b * 1e-3) / 1e9, "unit": "Gpixel/s", "ms_per_batch": ms_b,
+            "roofline": roofline_of(ops, ms_b), "hbm_gbs": nbytes / (ms_b * 1e-3) / 1e9,
             "plain_value": npx / (ms_p * 1e-3) / 1e9, "plain_ms_per_batch": ms_p,
             "speedup_vs_plain": ms_p / ms_b, "launch": launch, "graph_launches_per_batch": 1,
             "plain_launches_per_batch": len(frames)}
@@ -296,9 +312,12 @@ def run_fwd_bwd(args, dev):
     ev[1].record(stream)
     ev[1].synchronize()
     ms_b = ev[0].elapsed_time(ev[1]) / steps
+    ops_f = census(glint, sc)["ops"]
     return {"workload": "plane_sphere_fit 512x512, directional light, L2 loss vs perturbed-parameter target, "
                         "gradients w.r.t. alpha_x, alpha_y, ln density, light direction",
-            "ms_per_step": ms, "backward_ms": ms_b, "gpu_launches_per_step": 3,
+            "ms_per_step": ms, "backward_ms": ms_b, "gpu_launches_per_step": 3, "torch_launches_per_step": 2,
+            "roofline": roofline_of(ops_f * (2.0 + ADJOINT_FACTOR), ms),
+            "backward_roofline": roofline_of(ops_f * (1.0 + ADJOINT_FACTOR), ms_b),
             "grad": [float(x) for x in grad.cpu()]}
 
 

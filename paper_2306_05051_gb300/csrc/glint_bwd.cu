@@ -10,9 +10,10 @@
 // per-texel state is stored.  Within a cell the interpolation weights are
 // differentiated in difference form, e.g. for the simplex weights
 //   sum_j du_j X_j = (qx/2)(X1 - X0) + (qy/2)(X2 - X1)   (d q / d ln rho = q/2),
-// which avoids cancelling the large +-q/2 terms.  Per-thread gradients are
-// accumulated in FP64, reduced per CTA in a fixed order into the workspace,
-// and a second kernel sums the CTA partials in a fixed order: deterministic.
+// which avoids cancelling the large +-q/2 terms.  Per-pixel terms are formed
+// in FP32; each thread's sums over its pixels are FP64, reduced per CTA in a
+// fixed order into the workspace, and a second kernel sums the CTA partials
+// in a fixed order: deterministic.
 #include "glint_kernels.cuh"
 
 namespace glint {
@@ -139,16 +140,16 @@ __device__ void light_grad(const KParams& P, const FrameDesc& F, const PixelSetu
     }
 }
 
-// Relaxed value and gradient of one pixel (g[0..ng), FP64).  Returns the
-// relaxed radiance.
-__device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& F, int px, double* g, int ng) {
-    for (int k = 0; k < ng; ++k) g[k] = 0.0;
+// Relaxed radiance of one pixel; adds go * d(radiance)/d(theta) to mine[]
+// (FP64, the thread's running sums over its pixels).  The per-pixel terms
+// are formed in FP32.
+__device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& F, int px, double go,
+                            double* mine) {
     PixelSetup S;
     setup_pixel(P, T, F, px, S);
     if (S.status != 0) return 0.0f;
     float out = 0.0f;
-    double acc[kMaxGrad];
-    for (int k = 0; k < ng; ++k) acc[k] = 0.0;
+    float gm[3] = {0.0f, 0.0f, 0.0f};         // alpha_x, alpha_y, ln density
     for (int l = 0; l < F.nL; ++l) {
         LightState L;
         setup_light<true>(P, F, S, px, l, L);
@@ -161,10 +162,10 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
         float Z0[4] = {0, 0, 0, 0}, Z1[4] = {0, 0, 0, 0};
         for (int sub = 0; sub < S.K; ++sub) {
             SubState U;
-            if (!setup_sub<true>(P, T, S, sub, U, U.S0, U.uw, 1)) {
-                for (int k = 0; k < ng; ++k) g[k] = 0.0;
-                return 0.0f;
-            }
+            // the sub-footprints are the same for every light, so a
+            // coordinate out of range shows at the first light that is on,
+            // before this pixel has added anything to mine[]
+            if (!setup_sub<true>(P, T, S, sub, U, U.S0, U.uw, 1)) return 0.0f;
             for (int i = 0; i < 4; ++i) {
                 float X[3];
                 for (int j = 0; j < 3; ++j) {
@@ -193,8 +194,7 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
             }
         }
         // d C / d theta through the count parameters of each tetrahedron vertex
-        double dC[kMaxGrad];
-        for (int k = 0; k < ng; ++k) dC[k] = 0.0;
+        float dC[3] = {0.0f, 0.0f, 0.0f}, dCd[3] = {0.0f, 0.0f, 0.0f};
         const float p = L.p;
         for (int i = 0; i < 4; ++i) {
             const float n = S.ntr[i];
@@ -202,32 +202,33 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
             const float dnm1 = n > 1.0f ? S.dntr[i] : 0.0f;
             const float mu = law[i].mu, sig = law[i].sig;
             // d mu = nm1 dp + p dnm1;  d sigma = ((1 - p) d mu - mu dp) / (2 sigma)
-            auto add = [&](int k, float dp, float dn) {
+            auto term = [&](float dp, float dn) {
                 const float dmu = nm1 * dp + p * dn;
                 const float dsig = sig > 0.0f ? ((1.0f - p) * dmu - mu * dp) / (2.0f * sig) : 0.0f;
-                dC[k] += (double)dmu * Z0[i] + (double)dsig * Z1[i];
+                return dmu * Z0[i] + dsig * Z1[i];
             };
-            add(0, LG.dp_da[0], 0.0f);
-            add(1, LG.dp_da[1], 0.0f);
-            add(2, 0.0f, dnm1);
+            dC[0] += term(LG.dp_da[0], 0.0f);
+            dC[1] += term(LG.dp_da[1], 0.0f);
+            dC[2] += term(0.0f, dnm1);
             if (LG.dir)
-                for (int c = 0; c < 3; ++c) add(3 + 3 * l + c, LG.dp_dd[c], 0.0f);
+                for (int c = 0; c < 3; ++c) dCd[c] += term(LG.dp_dd[c], 0.0f);
         }
         dC[2] += Su;
-        if (LG.dir)
-            for (int c = 0; c < 3; ++c) dC[3 + 3 * l + c] += (double)Svx * LG.dfx_dd[c] + (double)Svy * LG.dfy_dd[c];
         // out_l = shade C / A;  d A / d ln rho = A
-        const double iA = 1.0 / (double)S.A.hi;
-        const double outl = (double)L.shade * C * iA;
-        out += (float)outl;
-        acc[0] += ((double)LG.ds_da[0] * C + (double)L.shade * dC[0]) * iA;
-        acc[1] += ((double)LG.ds_da[1] * C + (double)L.shade * dC[1]) * iA;
-        acc[2] += (double)L.shade * dC[2] * iA - outl;
-        if (LG.dir)
-            for (int c = 0; c < 3; ++c)
-                acc[3 + 3 * l + c] += ((double)LG.ds_dd[c] * C + (double)L.shade * dC[3 + 3 * l + c]) * iA;
+        const float iA = 1.0f / S.A.hi;
+        const float outl = L.shade * C * iA;
+        out += outl;
+        gm[0] += (LG.ds_da[0] * C + L.shade * dC[0]) * iA;
+        gm[1] += (LG.ds_da[1] * C + L.shade * dC[1]) * iA;
+        gm[2] += L.shade * dC[2] * iA - outl;
+        if (LG.dir && go != 0.0)
+            for (int c = 0; c < 3; ++c) {
+                const float dfv = Svx * LG.dfx_dd[c] + Svy * LG.dfy_dd[c];
+                mine[3 + 3 * l + c] += go * (double)((LG.ds_dd[c] * C + L.shade * (dCd[c] + dfv)) * iA);
+            }
     }
-    for (int k = 0; k < ng; ++k) g[k] = acc[k];
+    if (go != 0.0)
+        for (int k = 0; k < 3; ++k) mine[k] += go * (double)gm[k];
     return out;
 }
 
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
                                                           const float* grad_out, float* out_relaxed,
                                                           double* partial, int ng) {
     __shared__ Tables T;
-    __shared__ double red[kBwdThreads];
+    __shared__ double red[kBwdThreads / 32][kMaxGrad];
     const int nwords = (int)(sizeof(DfTables) / 4) + rot_entries(P.M) * (int)(sizeof(RotEntry) / 4);
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(&P.tables);
@@ -247,39 +248,41 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
     for (int k = 0; k < ng; ++k) mine[k] = 0.0;
     const int stride = gridDim.x * blockDim.x;
     for (int px = blockIdx.x * blockDim.x + threadIdx.x; px < F.npx; px += stride) {
-        double g[kMaxGrad];
-        const float o = pixel_grad(P, T, F, px, g, ng);
+        const float o = pixel_grad(P, T, F, px, (double)grad_out[px], mine);
         if (out_relaxed) out_relaxed[px] = o;
-        const double go = (double)grad_out[px];
-        if (go != 0.0)
-            for (int k = 0; k < ng; ++k) mine[k] += go * g[k];
     }
-    // fixed-order tree reduction of each component over the CTA
+    // fixed-order reduction over the CTA: a shuffle tree per warp, then the
+    // warps' sums in warp order
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int k = 0; k < ng; ++k) {
-        red[threadIdx.x] = mine[k];
-        __syncthreads();
-        for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ng + k] = red[0];
-        __syncthreads();
+        double v = mine[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[w][k] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < ng) {
+        double t = 0.0;
+        for (int ww = 0; ww < kBwdThreads / 32; ++ww) t += red[ww][threadIdx.x];
+        partial[(size_t)blockIdx.x * ng + threadIdx.x] = t;
     }
 }
 
-// grad[k] = sum over CTA partials, in CTA order.
+// grad[k] = sum over the CTA partials: warp k sums blocks lane, lane + 32,
+// ... in order, then a shuffle tree; a fixed order, so deterministic.
 __global__ void bwd_reduce_kernel(const double* partial, int nblocks, int ng, float* grad) {
-    const int k = threadIdx.x;
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k >= ng) return;
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * ng + k];
-    grad[k] = (float)s;
+    for (int b = lane; b < nblocks; b += 32) s += partial[(size_t)b * ng + k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) grad[k] = (float)s;
 }
 
+// One pixel per thread up to 8 CTAs per SM, then a grid-stride loop.
 int bwd_blocks(int npx) {
     const int sms = num_sms() > 0 ? num_sms() : 1;
     const int need = (npx + kBwdThreads - 1) / kBwdThreads;
-    const int cap = sms * 4;
+    const int cap = sms * 8;
     return need < cap ? need : cap;
 }
 
@@ -316,7 +319,7 @@ int glint_backward(const GlintFrame* frame, const GlintMaterial* material, const
     cudaStream_t s = (cudaStream_t)stream;
     bwd_kernel<<<blocks, kBwdThreads, 0, s>>>(P, F, grad_out, out_relaxed, static_cast<double*>(workspace), ng);
     if ((rc = cuda_rc(cudaGetLastError()))) return rc;
-    bwd_reduce_kernel<<<1, 32, 0, s>>>(static_cast<const double*>(workspace), blocks, ng, grad);
+    bwd_reduce_kernel<<<1, 32 * ng, 0, s>>>(static_cast<const double*>(workspace), blocks, ng, grad);
     return cuda_rc(cudaGetLastError());
 }
 
