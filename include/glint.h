@@ -144,8 +144,13 @@ int glint_eval_launch(const GlintFrame* frame, const GlintMaterial* material,
 /* The same evaluation with host buffers: copies every plane of `frame`
  * (host pointers, ideally pinned) into `staging` (device, caller-owned, at
  * least glint_eval_host_staging_size() bytes), evaluates, and copies the
- * image back to `out` (host).  The copies are enqueued on `stream`; the
- * caller synchronises before reading `out`. */
+ * image back to `out` (host).  The frame is processed in bands of about 1 M
+ * pixels of whole rows (at most 64 bands) so that copies in, kernels and
+ * copies out of different bands overlap: the copies run on two internal
+ * streams of the library (one pair per device, created on first use) that
+ * fork from and join back into `stream` through events.  Work enqueued on
+ * `stream` after the call sees the finished image; the caller synchronises
+ * `stream` before reading `out`.  Same image bits as glint_eval. */
 size_t glint_eval_host_staging_size(int32_t width, int32_t height, int32_t n_lights,
                                     int32_t has_light_plane, int32_t has_material_plane);
 int glint_eval_host(const GlintFrame* host_frame, const GlintMaterial* material,

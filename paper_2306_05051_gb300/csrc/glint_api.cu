@@ -153,6 +153,7 @@ FrameDesc make_frame_desc(const GlintFrame* f, float* out) {
     F.mat_px = reinterpret_cast<const float2*>(f->mat_px);
     F.out = out;
     F.W = f->width; F.H = f->height; F.npx = f->width * f->height; F.nL = f->n_lights;
+    F.lstride = F.npx;
     return F;
 }
 
@@ -196,6 +197,103 @@ int cuda_rc(cudaError_t e) {
     return GLINT_ERR_CUDA;
 }
 
+}  // namespace glint
+
+namespace glint {
+namespace {
+
+// Internal copy streams of the host-buffer path, one pair per device,
+// created on first use and kept for the life of the process.
+struct CopyStreams {
+    cudaStream_t h2d, d2h;
+};
+std::mutex g_copy_mutex;
+CopyStreams g_copy[64];
+
+int copy_streams(CopyStreams** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GLINT_ERR_CUDA;
+    if (dev < 0 || dev >= 64) return GLINT_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_copy_mutex);
+    CopyStreams& c = g_copy[dev];
+    if (!c.h2d && cudaStreamCreateWithFlags(&c.h2d, cudaStreamNonBlocking) != cudaSuccess) return GLINT_ERR_CUDA;
+    if (!c.d2h && cudaStreamCreateWithFlags(&c.d2h, cudaStreamNonBlocking) != cudaSuccess) return GLINT_ERR_CUDA;
+    *out = &c;
+    return GLINT_OK;
+}
+
+constexpr size_t kBandPixels = size_t(1) << 20;     // about 1 M pixels per band
+constexpr int kMaxBands = 64;
+
+// Copy in, shade and copy out a frame in bands of rows, so that the
+// host->device copy of band k+1, the kernel of band k and the device->host
+// copy of band k-1 overlap (copy engines in both directions and the SMs).
+// The caller's stream forks to the two internal copy streams through events
+// and joins them again before returning, so work queued on `s` afterwards
+// sees the finished image.  F: the whole frame in the staging buffer.
+int host_pipeline(const GlintFrame* hf, const KParams& P, const FrameDesc& F, float* out_host, cudaStream_t s) {
+    const size_t W = (size_t)hf->width, npx = (size_t)F.npx;
+    size_t rows = (kBandPixels + W - 1) / W;
+    if ((hf->height + rows - 1) / rows > (size_t)kMaxBands) rows = (hf->height + kMaxBands - 1) / kMaxBands;
+    const int nb = (int)((hf->height + rows - 1) / rows);
+    CopyStreams* cs = nullptr;
+    int rc = copy_streams(&cs);
+    if (rc) return rc;
+    cudaEvent_t ev[2 * kMaxBands + 2];
+    int nev = 0;
+    auto event = [&](cudaEvent_t* e) {
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return false;
+        ev[nev++] = *e;
+        return true;
+    };
+    auto fail = [&](int code) {
+        for (int k = 0; k < nev; ++k) cudaEventDestroy(ev[k]);     // released once complete
+        return code;
+    };
+    const char* hg = reinterpret_cast<const char*>(hf->gbuf);
+    const char* hl = reinterpret_cast<const char*>(hf->light_px);
+    const char* hm = reinterpret_cast<const char*>(hf->mat_px);
+    char* dg = reinterpret_cast<char*>(const_cast<float4*>(F.gbuf));
+    char* dl = reinterpret_cast<char*>(const_cast<float4*>(F.light_px));
+    char* dm = reinterpret_cast<char*>(const_cast<float2*>(F.mat_px));
+    cudaEvent_t start;
+    if (!event(&start)) return fail(GLINT_ERR_CUDA);
+    if (cudaEventRecord(start, s) != cudaSuccess || cudaStreamWaitEvent(cs->h2d, start, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(cs->d2h, start, 0) != cudaSuccess)
+        return fail(GLINT_ERR_CUDA);
+    for (int k = 0; k < nb; ++k) {
+        const size_t r0 = (size_t)k * rows;
+        const size_t r1 = r0 + rows < (size_t)hf->height ? r0 + rows : (size_t)hf->height;
+        const size_t b0 = r0 * W, n = (r1 - r0) * W;
+        bool ok = cudaMemcpyAsync(dg + b0 * 64, hg + b0 * 64, n * 64, cudaMemcpyHostToDevice, cs->h2d) == cudaSuccess;
+        if (hl)
+            for (int l = 0; l < hf->n_lights && ok; ++l)
+                ok = cudaMemcpyAsync(dl + (l * npx + b0) * 16, hl + (l * npx + b0) * 16, n * 16,
+                                     cudaMemcpyHostToDevice, cs->h2d) == cudaSuccess;
+        if (hm && ok) ok = cudaMemcpyAsync(dm + b0 * 8, hm + b0 * 8, n * 8, cudaMemcpyHostToDevice, cs->h2d) == cudaSuccess;
+        cudaEvent_t in, done;
+        if (!ok || !event(&in) || !event(&done)) return fail(GLINT_ERR_CUDA);
+        if (cudaEventRecord(in, cs->h2d) != cudaSuccess || cudaStreamWaitEvent(s, in, 0) != cudaSuccess)
+            return fail(GLINT_ERR_CUDA);
+        FrameDesc Fk = F;
+        Fk.gbuf = F.gbuf + b0 * 4;
+        if (F.light_px) Fk.light_px = F.light_px + b0;
+        if (F.mat_px) Fk.mat_px = F.mat_px + b0;
+        Fk.out = F.out + b0;
+        Fk.npx = (int)n;
+        Fk.H = (int)(r1 - r0);
+        if ((rc = cuda_rc(launch_fwd(P, Fk, s, default_fwd_launch(Fk.npx))))) return fail(rc);
+        if (cudaEventRecord(done, s) != cudaSuccess || cudaStreamWaitEvent(cs->d2h, done, 0) != cudaSuccess ||
+            cudaMemcpyAsync(out_host + b0, F.out + b0, n * 4, cudaMemcpyDeviceToHost, cs->d2h) != cudaSuccess)
+            return fail(GLINT_ERR_CUDA);
+    }
+    cudaEvent_t end;
+    if (!event(&end) || cudaEventRecord(end, cs->d2h) != cudaSuccess || cudaStreamWaitEvent(s, end, 0) != cudaSuccess)
+        return fail(GLINT_ERR_CUDA);
+    return fail(GLINT_OK);
+}
+
+}  // namespace
 }  // namespace glint
 
 using namespace glint;
@@ -266,31 +364,23 @@ int glint_eval_host(const GlintFrame* hf, const GlintMaterial* material, const G
     if ((rc = check_device_ptr(staging, 256))) return rc;
     const size_t npx = (size_t)hf->width * hf->height;
     char* base = static_cast<char*>(staging);
-    cudaStream_t s = (cudaStream_t)stream;
     GlintFrame df_ = *hf;
     size_t off = 0;
     df_.gbuf = reinterpret_cast<const float*>(base + off);
-    if (cudaMemcpyAsync(base + off, hf->gbuf, npx * 64, cudaMemcpyHostToDevice, s) != cudaSuccess) return GLINT_ERR_CUDA;
     off += align256(npx * 64);
     if (hf->light_px) {
         df_.light_px = reinterpret_cast<const float*>(base + off);
-        if (cudaMemcpyAsync(base + off, hf->light_px, npx * 16 * hf->n_lights, cudaMemcpyHostToDevice, s) != cudaSuccess)
-            return GLINT_ERR_CUDA;
         off += align256(npx * 16 * (size_t)hf->n_lights);
     }
     if (hf->mat_px) {
         df_.mat_px = reinterpret_cast<const float*>(base + off);
-        if (cudaMemcpyAsync(base + off, hf->mat_px, npx * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
-            return GLINT_ERR_CUDA;
         off += align256(npx * 8);
     }
     float* dout = reinterpret_cast<float*>(base + off);
     KParams P;
     FrameDesc F;
     if ((rc = make_params(&df_, material, lights, dout, &P, &F))) return rc;
-    if ((rc = cuda_rc(launch_fwd(P, F, s, default_fwd_launch(F.npx))))) return rc;
-    if (cudaMemcpyAsync(out_host, dout, npx * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return GLINT_ERR_CUDA;
-    return GLINT_OK;
+    return host_pipeline(hf, P, F, out_host, (cudaStream_t)stream);
 }
 
 int glint_eval_trace(const GlintFrame* frame, const GlintMaterial* material, const GlintLight* lights,

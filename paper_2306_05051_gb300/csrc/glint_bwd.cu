@@ -60,7 +60,7 @@ __device__ void light_grad(const KParams& P, const FrameDesc& F, const PixelSetu
     G.dir = kl.kind == 1;
     float d[3];
     if (kl.kind == 0) {
-        const float4 lp = __ldg(F.light_px + (size_t)l * F.npx + px);
+        const float4 lp = __ldg(F.light_px + (size_t)l * F.lstride + px);
         d[0] = lp.x; d[1] = lp.y; d[2] = lp.z;
     } else {
         d[0] = kl.dx; d[1] = kl.dy; d[2] = kl.dz;
@@ -125,7 +125,7 @@ __device__ void light_grad(const KParams& P, const FrameDesc& F, const PixelSetu
     const float Gs = 1.0f / ((1.0f + lam_v) * (1.0f + lam_l));
     const float Dn = 1.0f / (3.14159265358979f * ax * ay);
     float E;
-    if (kl.kind == 0) E = __ldg(F.light_px + (size_t)l * F.npx + px).w; else E = kl.E;
+    if (kl.kind == 0) E = __ldg(F.light_px + (size_t)l * F.lstride + px).w; else E = kl.E;
     const float base = Dn * E / (4.0f * P.R * S.cos_v);
     for (int c = 0; c < 2; ++c) {
         const float dG = -Gs * (dlv_da[c] / (1.0f + lam_v) + dll_da[c] / (1.0f + lam_l));

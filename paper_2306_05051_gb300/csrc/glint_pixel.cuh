@@ -58,6 +58,7 @@ struct FrameDesc {
     const float2* mat_px;
     float* out;
     int32_t W, H, npx, nL;
+    int32_t lstride;             // pixels between the planes of consecutive lights (npx, or more for a band)
 };
 
 // Material, lights and tables, shared by every frame of a launch.
@@ -397,7 +398,7 @@ static __device__ __forceinline__ void setup_light(const KParams& P, const Frame
     const KLight kl = P.lights[l];
     float lr[3], E;
     if (kl.kind == 0) {
-        const float4 lp = __ldg(F.light_px + (size_t)l * F.npx + px);
+        const float4 lp = __ldg(F.light_px + (size_t)l * F.lstride + px);
         lr[0] = lp.x; lr[1] = lp.y; lr[2] = lp.z; E = lp.w;
     } else {
         lr[0] = kl.dx; lr[1] = kl.dy; lr[2] = kl.dz; E = kl.E;

@@ -146,6 +146,31 @@ def test_host_buffer_path_matches_device_path(orc):
     assert torch.equal(out, dev_img)
 
 
+@pytest.mark.parametrize("which", ["sphere_plane_tall", "grazing_plane"])
+def test_host_buffer_path_in_bands_matches_device_path(which):
+    """Frames of several bands (the last one short), with and without the
+    light and material planes: the banded, overlapped host path gives the
+    device path's bits, and the stream it was given is ordered after it."""
+    if which == "sphere_plane_tall":
+        sc = scenes.sphere_plane(1280, 2000, seed=11)          # 3 bands: 820, 820, 360 rows
+    else:
+        sc = scenes.grazing_plane()                           # 1920 x 1080, directional light, 2 bands
+    scd = sc.to(DEV)
+    dev_img = glint.render_scene(scd).cpu()
+    pin = lambda t: None if t is None else t.pin_memory()
+    host = scenes.Scene(sc.name, pin(sc.gbuf), pin(sc.light_px), pin(sc.mat_px), sc.material, sc.lights)
+    staging = torch.empty(glint.staging_bytes(host), dtype=torch.uint8, device=DEV)
+    out = torch.full((sc.height, sc.width), -1.0, dtype=torch.float32).pin_memory()
+    s = torch.cuda.Stream()
+    glint.render_host(host, staging, out, stream=s)
+    flag = torch.zeros(1, device=DEV)
+    with torch.cuda.stream(s):
+        flag += 1.0                                            # queued after the call on the same stream
+    s.synchronize()
+    assert torch.equal(out, dev_img)
+    assert flag.item() == 1.0
+
+
 def test_side_stream_and_repeatability(orc):
     sc = scenes.plane45(128, 96)
     scd = sc.to(DEV)
