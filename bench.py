@@ -162,10 +162,33 @@ def frame_bytes(sc):
     return b
 
 
+def rank_frame(rank, world):
+    """(azimuth in degrees, seed) of the frame that rank `rank` of `world`
+    shades: the ranks split one orbit of the 4K scene, one frame each (weak
+    scaling; frames are independent, so no collective on the data path)."""
+    return 360.0 * rank / max(world, 1), 3 + rank
+
+
+def max_over_ranks(x, device):
+    """The slowest rank's time (all-reduce MAX); x itself with one rank."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()) or \
+            torch.distributed.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(npx_per_rank, world, ms_max):
+    """Gpixel/s of the whole job: every rank's pixels over the slowest rank's time."""
+    return npx_per_rank * world / (ms_max * 1e-3) / 1e9
+
+
 def run_ours(args, rank, world, dev):
     from paper_2306_05051_gb300 import glint, scenes
     torch.cuda.set_device(dev)
-    scd = scenes.sphere_plane(azimuth_deg=360.0 * rank / max(world, 1), seed=3 + rank, device=dev)
+    az, seed = rank_frame(rank, world)
+    scd = scenes.sphere_plane(azimuth_deg=az, seed=seed, device=dev)
     npx = scd.width * scd.height
     out = torch.empty(scd.height, scd.width, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -186,11 +209,7 @@ def run_ours(args, rank, world, dev):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1) / args.steps
-    ms_all = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_all = float(t.item())
+    ms_all = max_over_ranks(ms, dev)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     host = scenes.Scene(scd.name, scd.gbuf.cpu().pin_memory(), scd.light_px.cpu().pin_memory(),
@@ -390,7 +409,7 @@ def main():
         torch.distributed.destroy_process_group() if world > 1 else None
         return
     npx_all = r["npx"] * world
-    value = npx_all / (r["ms"] * 1e-3) / 1e9
+    value = whole_job_rate(r["npx"], world, r["ms"])
     peaks = _peaks()
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = SMS * LANES_PER_SM * mhz * 1e6 / 1e12          # T lane-ops/s
