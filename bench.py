@@ -340,12 +340,13 @@ def run_fwd_bwd(args, dev):
             "grad": [float(x) for x in grad.cpu()]}
 
 
-def cpu_baseline(seconds=12.0):
+def cpu_baseline(seconds=12.0, sc=None):
     """The FP64 oracle on the host cores on a deterministic row sample of the
     same 4K frame (every 64th row, then further rows until ~seconds)."""
     import oracle
     from paper_2306_05051_gb300 import scenes
-    sc = scenes.sphere_plane(device="cpu")
+    if sc is None:
+        sc = scenes.sphere_plane(device="cpu")
     W, H = sc.width, sc.height
     cores = os.cpu_count() or 1
     rows = [r for phase in range(64) for r in range(phase, H, 64)]     # interleaved, deterministic
@@ -382,12 +383,16 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        from paper_2306_05051_gb300 import scenes
+        sc = scenes.sphere_plane(device="cpu")
+        # each step a bounded row sample, sized so the whole run takes ~2 minutes
+        per_step = min(4.0, max(0.05, 120.0 / (args.steps + args.warmup)))
         steps = []
         cb = None
         for _ in range(args.warmup):
-            cpu_baseline(0.5)
+            cpu_baseline(per_step, sc)
         for _ in range(args.steps):
-            cb = cpu_baseline(4.0)
+            cb = cpu_baseline(per_step, sc)
             steps.append(cb["value"])
         val = statistics.median(steps)
         cb["value"] = val
