@@ -129,8 +129,8 @@ int glint_eval(const GlintFrame* frame, const GlintMaterial* material,
  * pixels) and CTAs per SM.  ctas_per_sm = 0 (glint_eval's default, with 512
  * threads): one CTA per tile, the hardware scheduler balances tiles of
  * uneven cost over the SMs.  ctas_per_sm = 1..16: a persistent grid of
- * min(tiles, SMs x ctas_per_sm) CTAs loops over the tiles.  The batched
- * path (glint_ctx_set_launch) is always persistent and takes 1..16. */
+ * min(tiles, SMs x ctas_per_sm) CTAs loops over the tiles (the batched
+ * path's CTAs then take tiles from the context's counter). */
 typedef struct GlintLaunch {
     int32_t threads_per_cta;
     int32_t ctas_per_sm;

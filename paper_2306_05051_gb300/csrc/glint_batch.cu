@@ -27,7 +27,7 @@ struct GlintContext {
 namespace glint {
 namespace {
 
-const GlintLaunch kCandidates[] = {{256, 4}, {256, 8}, {512, 2}, {512, 4}, {1024, 1}, {1024, 2}};
+const GlintLaunch kCandidates[] = {{512, 0}, {256, 0}, {1024, 0}, {256, 4}, {256, 8}, {512, 2}, {1024, 1}};
 
 uint64_t batch_signature(const GlintFrame* frames, int n) {
     uint64_t h = 1469598103934665603ull;
@@ -46,6 +46,7 @@ uint64_t batch_signature(const GlintFrame* frames, int n) {
 void fill_batch(GlintContext* c, const GlintFrame* frames, int n, float* const* outs, int threads) {
     BatchDesc& B = c->B;
     B.n = n;
+    B.persistent = c->launch.ctas_per_sm > 0;
     B.counter = c->counter;
     int t = 0;
     for (int f = 0; f < n; ++f) {
@@ -59,6 +60,7 @@ void fill_batch(GlintContext* c, const GlintFrame* frames, int n, float* const* 
 FwdLaunch batch_launch(const BatchDesc& B, GlintLaunch L) {
     const int sms = num_sms() > 0 ? num_sms() : 1;
     const int tiles = B.tile_base[B.n];
+    if (L.ctas_per_sm == 0) return FwdLaunch{L.threads_per_cta, tiles};
     const int cap = sms * L.ctas_per_sm;
     return FwdLaunch{L.threads_per_cta, tiles < cap ? tiles : cap};
 }
@@ -181,7 +183,7 @@ int glint_ctx_get_launch(const GlintContext* c, GlintLaunch* out) {
 int glint_ctx_set_launch(GlintContext* c, const GlintLaunch* in) {
     if (!c || !in) return GLINT_ERR_ARG;
     const int t = in->threads_per_cta;
-    if ((t != 128 && t != 256 && t != 512 && t != 1024) || in->ctas_per_sm < 1 || in->ctas_per_sm > 16)
+    if ((t != 128 && t != 256 && t != 512 && t != 1024) || in->ctas_per_sm < 0 || in->ctas_per_sm > 16)
         return GLINT_ERR_ARG;
     c->launch = *in;
     c->tuned = true;

@@ -146,7 +146,7 @@ __device__ void light_grad(const KParams& P, const FrameDesc& F, const PixelSetu
 __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& F, int px, double go,
                             double* mine) {
     PixelSetup S;
-    setup_pixel(P, T, F, px, S);
+    setup_pixel<true>(P, T, F, px, S);
     if (S.status != 0) return 0.0f;
     float out = 0.0f;
     float gm[3] = {0.0f, 0.0f, 0.0f};         // alpha_x, alpha_y, ln density

@@ -78,7 +78,7 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
     PixelSetup S;
     S.status = 1;
     S.K = 0;
-    if (valid) setup_pixel(P, T, F, px, S);
+    if (valid) setup_pixel<false>(P, T, F, px, S);
     LightState ls[kMaxLights];
     for (int l = 0; l < F.nL; ++l) {
         ls[l].on = false;
@@ -184,9 +184,10 @@ __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KPara
     }
 }
 
-// Persistent kernel over the tiles of many frames: CTAs take tiles from a
-// global counter (reset to 0 before the launch); tile t belongs to frame f
-// with tile_base[f] <= t < tile_base[f+1].
+// Kernel over the tiles of many frames; tile t belongs to frame f with
+// tile_base[f] <= t < tile_base[f+1].  Persistent: CTAs take tiles from a
+// global counter (reset to 0 before the launch).  Otherwise one CTA per tile
+// (CTA b shades tile b), scheduled by the hardware.
 __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KParams P,
                                                      const __grid_constant__ BatchDesc B) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -197,9 +198,10 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KPa
     __shared__ int tile_s;
     load_tables(P, T);
     WarpQueue& q = Qs[threadIdx.x >> 5];
-    for (;;) {
+    for (int it = 0;; ++it) {
         __syncthreads();
-        if (threadIdx.x == 0) tile_s = (int)atomicAdd(B.counter, 1u);
+        if (threadIdx.x == 0)
+            tile_s = B.persistent ? (int)atomicAdd(B.counter, 1u) : (it == 0 ? (int)blockIdx.x : 0x7fffffff);
         __syncthreads();
         const int t = tile_s;
         if (t >= B.tile_base[B.n]) break;
@@ -225,7 +227,7 @@ size_t fwd_smem_bytes(int threads) {
 __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& F, int px, GlintTracePix* pr,
                             GlintTraceRec* recs, int cap) {
     PixelSetup S;
-    setup_pixel(P, T, F, px, S);
+    setup_pixel<true>(P, T, F, px, S);
     pr->status = S.status; pr->K = S.status == 0 ? S.K : 0; pr->n_rec = 0; pr->pad = 0;
     pr->A = S.status == 0 ? S.A.hi : 0.0f; pr->r = S.status == 0 ? S.ratio.hi : 0.0f;
     pr->phi = S.status == 0 ? S.phi.hi : 0.0f; pr->out = 0.0f;

@@ -19,6 +19,7 @@ constexpr int kMaxBatch = 128;
 // parameter, so a graph node can be re-pointed without re-capture).
 struct BatchDesc {
     int32_t n;
+    int32_t persistent;                 // 1: CTAs take tiles from the counter; 0: CTA b shades tile b
     uint32_t* counter;                  // tile counter, zero at launch
     int32_t tile_base[kMaxBatch + 1];   // first tile of each frame; tile_base[n] = total
     FrameDesc frames[kMaxBatch];

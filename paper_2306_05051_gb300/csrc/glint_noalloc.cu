@@ -76,6 +76,7 @@ extern "C" int glint_eval_batch_noalloc(const GlintFrame* frames, int32_t n_fram
         const int f0 = c * kMaxBatch;
         const int n = n_frames - f0 < kMaxBatch ? n_frames - f0 : kMaxBatch;
         B.n = n;
+        B.persistent = 1;
         B.counter = scratch + c;
         long long t = 0;
         for (int k = 0; k < n; ++k) {

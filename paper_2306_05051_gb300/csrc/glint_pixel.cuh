@@ -186,8 +186,11 @@ __device__ __forceinline__ bool load_gbuf(const FrameDesc& F, int px, float4& g0
     return finite;
 }
 
+// kTrace: also store what only the trace and adjoint kernels read (d ntr /
+// d ln density).
+template <bool kTrace>
 static __device__ __forceinline__ void setup_pixel(const KParams& P, const Tables& T, const FrameDesc& F, int px,
-                                               PixelSetup& S) {
+                                                   PixelSetup& S) {
     S.status = 2;
     S.K = 0;
     float4 g0, g1, g2, g3;
@@ -318,61 +321,57 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
     df t;
     int a = dffloor(scale2(S.phi * ldf(T.d.inv_pi), m == 0 ? 2 : m + 1), &t);
     a %= nm;
-    Vert tv[3];
-    df lam[3];
+    // triangle vertices (ring, orientation) and barycentrics; scalars, not
+    // arrays, so nothing below is indexed at run time
+    int r0, k0, r1, k1, r2, k2;
+    df lam0, lam1, lam2;
     if (m == 0) {
-        tv[0] = {0, 0, 0}; tv[1] = {1, a, 0}; tv[2] = {1, (a + 1) & 3, 0};
-        lam[0] = 1.0f - x;
-        lam[1] = x * (1.0f - t);
-        lam[2] = x * t;
+        r0 = 0; k0 = 0; r1 = 1; k1 = a; r2 = 1; k2 = (a + 1) & 3;
+        lam0 = 1.0f - x;
+        lam1 = x * (1.0f - t);
+        lam2 = x * t;
     } else {
-        const Vert P00 = {m, a, 0}, P01 = {m, (a + 1) % nm, 0};
-        const Vert P10 = {m + 1, 2 * a, 0}, P1h = {m + 1, 2 * a + 1, 0}, P11 = {m + 1, (2 * a + 2) % (2 * nm), 0};
+        // P00 = (m, a), P01 = (m, a + 1), P10 = (m + 1, 2a), P1h = (m + 1, 2a + 1), P11 = (m + 1, 2a + 2)
+        const int a01 = (a + 1) % nm, a11 = (2 * a + 2) % (2 * nm);
         const df xh = scale2(x, -1);
-        if (dfle(t, xh)) {
-            tv[0] = P00; tv[1] = P10; tv[2] = P1h;
-            lam[0] = 1.0f - x; lam[1] = x - scale2(t, 1); lam[2] = scale2(t, 1);
-        } else if (dfle(t, 1.0f - xh)) {
-            tv[0] = P00; tv[1] = P1h; tv[2] = P01;
-            lam[0] = (1.0f - t) - xh; lam[1] = x; lam[2] = t - xh;
-        } else {
+        if (dfle(t, xh)) {                                 // P00, P10, P1h
+            r0 = m; k0 = a; r1 = m + 1; k1 = 2 * a; r2 = m + 1; k2 = 2 * a + 1;
+            lam0 = 1.0f - x; lam1 = x - scale2(t, 1); lam2 = scale2(t, 1);
+        } else if (dfle(t, 1.0f - xh)) {                   // P00, P1h, P01
+            r0 = m; k0 = a; r1 = m + 1; k1 = 2 * a + 1; r2 = m; k2 = a01;
+            lam0 = (1.0f - t) - xh; lam1 = x; lam2 = t - xh;
+        } else {                                           // P1h, P01, P11
             const df omt = 1.0f - t;
-            tv[0] = P1h; tv[1] = P01; tv[2] = P11;
-            lam[0] = scale2(omt, 1); lam[1] = 1.0f - x; lam[2] = x - scale2(omt, 1);
+            r0 = m + 1; k0 = 2 * a + 1; r1 = m; k1 = a01; r2 = m + 1; k2 = a11;
+            lam0 = scale2(omt, 1); lam1 = 1.0f - x; lam2 = x - scale2(omt, 1);
         }
     }
-    // prism split by vertex order: upper weight of vertex j = clamp(s - C_j, 0, lam_j)
-    int vtri[4], vup[4];
-    df w[4];
-    const df C1 = lam[0], C2 = lam[0] + lam[1];
-    if (dfle(s, C1)) {
-        vtri[0] = 0; vup[0] = 0; w[0] = lam[0] - s;
-        vtri[1] = 1; vup[1] = 0; w[1] = lam[1];
-        vtri[2] = 2; vup[2] = 0; w[2] = lam[2];
-        vtri[3] = 0; vup[3] = 1; w[3] = s;
-    } else if (dfle(s, C2)) {
-        vtri[0] = 1; vup[0] = 0; w[0] = lam[1] - (s - C1);
-        vtri[1] = 2; vup[1] = 0; w[1] = lam[2];
-        vtri[2] = 0; vup[2] = 1; w[2] = lam[0];
-        vtri[3] = 1; vup[3] = 1; w[3] = s - C1;
-    } else {
-        vtri[0] = 2; vup[0] = 0; w[0] = lam[2] - (s - C2);
-        vtri[1] = 0; vup[1] = 1; w[1] = lam[0];
-        vtri[2] = 1; vup[2] = 1; w[2] = lam[1];
-        vtri[3] = 2; vup[3] = 1; w[3] = s - C2;
-    }
+    // Prism split by vertex order: upper weight of vertex j = clamp(s - C_j,
+    // 0, lam_j), C_0 = 0, C_1 = lam_0, C_2 = lam_0 + lam_1.  With c the
+    // interval of s, tetrahedron vertex i sits on triangle vertex (c + i) mod 3,
+    // on the upper LOD for i >= 3 - c; its weights are
+    // (lam_c - (s - C_c), lam_{c+1}, lam_{c+2}, s - C_c).
+    const df C1 = lam0, C2 = lam0 + lam1;
+    const int c = dfle(s, C1) ? 0 : (dfle(s, C2) ? 1 : 2);
+    const df sc = c == 0 ? s : (c == 1 ? s - C1 : s - C2);
+    const df lc = c == 0 ? lam0 : (c == 1 ? lam1 : lam2);
+    const df w[4] = {lc - sc, c == 0 ? lam1 : (c == 1 ? lam2 : lam0), c == 0 ? lam2 : (c == 1 ? lam0 : lam1), sc};
     // d s / d ln(density) = A_s / (f^l (f - 1)); the first tetrahedron vertex
     // loses and the last gains weight with s (every tetrahedron), the middle
     // two do not depend on s.  Pinned: n_i = w_i A_s.
     const float ds = pinned ? 0.0f : scale2(As, -level * P.log2f).hi / (float)(P.f - 1);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        S.vert[i] = tv[vtri[i]];
-        S.vert[i].level = level + vup[i];
+        const int k = (c + i) % 3;
+        S.vert[i].ring = k == 0 ? r0 : (k == 1 ? r1 : r2);
+        S.vert[i].kor = k == 0 ? k0 : (k == 1 ? k1 : k2);
+        S.vert[i].level = level + (i >= 3 - c ? 1 : 0);
         const df ni = pinned ? w[i] * As : scale2(w[i], S.vert[i].level * P.log2f);
         S.ntr[i] = ni.hi;
-        const float dw = i == 0 ? -ds : (i == 3 ? ds : 0.0f);
-        S.dntr[i] = pinned ? ni.hi : dw * pow2f((S.vert[i].level) * P.log2f);
+        if (kTrace) {
+            const float dw = i == 0 ? -ds : (i == 3 ? ds : 0.0f);
+            S.dntr[i] = pinned ? ni.hi : dw * pow2f((S.vert[i].level) * P.log2f);
+        }
     }
     S.status = 0;
 }

@@ -52,7 +52,7 @@ def test_batch_fixed_launch_shapes_and_reuse():
     fr = _frames(6)
     ref = [glint.render_scene(s) for s in fr]
     ctx = glint.BatchContext(DEV)
-    for shape in [(128, 8), (256, 4), (1024, 1)]:
+    for shape in [(128, 8), (256, 4), (1024, 1), (512, 0), (256, 0), (512, 2), (128, 0)]:
         ctx.launch = shape
         outs = ctx.render(fr)
         torch.cuda.synchronize()
@@ -95,6 +95,6 @@ def test_batch_argument_errors():
     assert L.glint_eval_batch(ctx._h, frames, 0, C.byref(mat), lts, optr, None) == -1
     assert L.glint_eval_batch(ctx._h, frames, 129, C.byref(mat), lts, optr, None) == -1
     assert L.glint_eval_batch(None, frames, 1, C.byref(mat), lts, optr, None) == -1
-    bad = _lib.GlintLaunch(100, 2)
-    assert L.glint_ctx_set_launch(ctx._h, C.byref(bad)) == -1
+    for bad in [(100, 2), (512, -1), (512, 17)]:
+        assert L.glint_ctx_set_launch(ctx._h, C.byref(_lib.GlintLaunch(*bad))) == -1
     ctx.close()
