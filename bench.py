@@ -331,12 +331,24 @@ def run_fwd_bwd(args, dev):
     ev[1].record(stream)
     ev[1].synchronize()
     ms_b = ev[0].elapsed_time(ev[1]) / steps
+    # the same step as one glint_fit_l2 pass (image, L2 loss and gradient)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        glint.fit_l2(sc, timg, stream=stream, workspace=ws, out=img, grad=grad, loss=loss)
+    ev[0].record(stream)
+    for _ in range(steps):
+        glint.fit_l2(sc, timg, stream=stream, workspace=ws, out=img, grad=grad, loss=loss)
+    ev[1].record(stream)
+    ev[1].synchronize()
+    ms_fused = ev[0].elapsed_time(ev[1]) / steps
     ops_f = census(glint, sc)["ops"]
     return {"workload": "plane_sphere_fit 512x512, directional light, L2 loss vs perturbed-parameter target, "
                         "gradients w.r.t. alpha_x, alpha_y, ln density, light direction",
             "ms_per_step": ms, "backward_ms": ms_b, "gpu_launches_per_step": 3, "torch_launches_per_step": 2,
             "roofline": roofline_of(ops_f * (2.0 + ADJOINT_FACTOR), ms),
             "backward_roofline": roofline_of(ops_f * (1.0 + ADJOINT_FACTOR), ms_b),
+            "fused_ms_per_step": ms_fused, "fused_launches_per_step": 2,
+            "fused_roofline": roofline_of(ops_f * (2.0 + ADJOINT_FACTOR), ms_fused),
             "grad": [float(x) for x in grad.cpu()]}
 
 

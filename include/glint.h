@@ -209,6 +209,26 @@ int glint_backward(const GlintFrame* frame, const GlintMaterial* material, const
                    const float* grad_out, float* grad, float* out_relaxed,
                    void* workspace, size_t workspace_bytes, void* stream);
 
+/* One pass of an L2 image fit: the image, the loss and its gradient, without
+ * a separate forward launch.  Per pixel the kernel evaluates the image value
+ * out[px] (integer counts, as glint_eval; equal to glint_eval's image up to
+ * the order of the floating-point sum, ~1e-7 relative), the relaxed value
+ * and its derivatives, and weights the derivatives by 2 (out[px] -
+ * target[px]): the loss of an L2 fit depends on each pixel's own value only,
+ * so grad_out of glint_backward is known inside the pixel.
+ *   grad[k] = sum_px 2 (out[px] - target[px]) d relaxed(px) / d theta_k
+ *   *loss   = sum_px (out[px] - target[px])^2      (FP64 sums, deterministic)
+ * The paper fits nothing: this entry point serves the differentiable use of
+ * the model (material and light fitting against a target image).
+ *   target: device [height][width] float.   out: device [height][width] float.
+ *   grad:   device, 3 + 3 * n_lights floats.  loss: device float or NULL.
+ *   workspace: as glint_backward.
+ * Requires the scalar material (frame->mat_px == NULL), else
+ * GLINT_ERR_UNSUPPORTED; a small workspace gives GLINT_ERR_WORKSPACE. */
+int glint_fit_l2(const GlintFrame* frame, const GlintMaterial* material, const GlintLight* lights,
+                 const float* target, float* out, float* grad, float* loss,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
 /* glint_eval_batch for callers that cannot allocate device memory.  The paper
  * has no counterpart: this is an interface for hosts that own every
  * allocation - a renderer with a fixed memory budget, code that must not

@@ -70,6 +70,7 @@ SIGNATURES = {
     "glint_eval_batch_noalloc": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "glint_backward_workspace_size": (C.c_size_t, [_P]),
     "glint_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "glint_fit_l2": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
 }
 
 

@@ -140,15 +140,17 @@ __device__ void light_grad(const KParams& P, const FrameDesc& F, const PixelSetu
     }
 }
 
-// Relaxed radiance of one pixel; adds go * d(radiance)/d(theta) to mine[]
-// (FP64, the thread's running sums over its pixels).  The per-pixel terms
-// are formed in FP32.
-__device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& F, int px, double go,
-                            double* mine) {
+// One pixel: returns the relaxed radiance, writes d(relaxed)/d(theta) to
+// g[0..ng) (FP32) and the radiance with integer counts (the image's value)
+// to *disc.
+__device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& F, int px, float* g, int ng,
+                            float* disc) {
+    for (int k = 0; k < ng; ++k) g[k] = 0.0f;
+    *disc = 0.0f;
     PixelSetup S;
     setup_pixel<true>(P, T, F, px, S);
     if (S.status != 0) return 0.0f;
-    float out = 0.0f;
+    float out = 0.0f, outd = 0.0f;
     float gm[3] = {0.0f, 0.0f, 0.0f};         // alpha_x, alpha_y, ln density
     for (int l = 0; l < F.nL; ++l) {
         LightState L;
@@ -158,19 +160,22 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
         light_grad(P, F, S, px, l, L, LG);
         CountLaw law[4];
         for (int i = 0; i < 4; ++i) law[i] = count_law(S.ntr[i], L.p, L.lq);
-        float C = 0.0f, Su = 0.0f, Svx = 0.0f, Svy = 0.0f;
+        float C = 0.0f, Cd = 0.0f, Su = 0.0f, Svx = 0.0f, Svy = 0.0f;
         float Z0[4] = {0, 0, 0, 0}, Z1[4] = {0, 0, 0, 0};
         for (int sub = 0; sub < S.K; ++sub) {
             SubState U;
             // the sub-footprints are the same for every light, so a
             // coordinate out of range shows at the first light that is on,
             // before this pixel has added anything to mine[]
-            if (!setup_sub<true>(P, T, S, sub, U, U.S0, U.uw, 1)) return 0.0f;
+            if (!setup_sub<true>(P, T, S, sub, U, U.S0, U.uw, 1)) {
+                for (int k = 0; k < ng; ++k) g[k] = 0.0f;
+                return 0.0f;
+            }
             for (int i = 0; i < 4; ++i) {
                 float X[3];
                 for (int j = 0; j < 3; ++j) {
                     float ct[4];
-                    float z0 = 0.0f, z1 = 0.0f;
+                    float z0 = 0.0f, z1 = 0.0f, xd = 0.0f;
                     for (int k = 0; k < 4; ++k) {
                         ct[k] = 0.0f;
                         const uint32_t h0 = fmix32(U.S0[3 * i + j] + L.A0[k]);
@@ -178,12 +183,14 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
                             const float z = normal_of_word(fmix32(U.S1[3 * i + j] + L.A1[k]));
                             const float cc = 1.0f + law[i].mu + law[i].sig * z;
                             ct[k] = fminf(fmaxf(cc, 1.0f), law[i].nceil);
+                            xd += L.v[k] * fminf(fmaxf(floorf(cc), 1.0f), law[i].nceil);
                             if (cc > 1.0f && cc < law[i].nceil) { z0 += L.v[k]; z1 += L.v[k] * z; }
                         }
                     }
                     X[j] = L.v[0] * ct[0] + L.v[1] * ct[1] + L.v[2] * ct[2] + L.v[3] * ct[3];
                     const float u = U.uw[3 * i + j];
                     C += u * X[j];
+                    Cd += u * xd;
                     Svx += u * ((1.0f - LG.fy) * (ct[1] - ct[0]) + LG.fy * (ct[3] - ct[2]));
                     Svy += u * ((1.0f - LG.fx) * (ct[2] - ct[0]) + LG.fx * (ct[3] - ct[1]));
                     Z0[i] += u * z0;
@@ -218,25 +225,31 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
         const float iA = 1.0f / S.A.hi;
         const float outl = L.shade * C * iA;
         out += outl;
+        outd += L.shade * Cd * iA;
         gm[0] += (LG.ds_da[0] * C + L.shade * dC[0]) * iA;
         gm[1] += (LG.ds_da[1] * C + L.shade * dC[1]) * iA;
         gm[2] += L.shade * dC[2] * iA - outl;
-        if (LG.dir && go != 0.0)
+        if (LG.dir)
             for (int c = 0; c < 3; ++c) {
                 const float dfv = Svx * LG.dfx_dd[c] + Svy * LG.dfy_dd[c];
-                mine[3 + 3 * l + c] += go * (double)((LG.ds_dd[c] * C + L.shade * (dCd[c] + dfv)) * iA);
+                g[3 + 3 * l + c] = (LG.ds_dd[c] * C + L.shade * (dCd[c] + dfv)) * iA;
             }
     }
-    if (go != 0.0)
-        for (int k = 0; k < 3; ++k) mine[k] += go * (double)gm[k];
+    for (int k = 0; k < 3; ++k) g[k] = gm[k];
+    *disc = outd;
     return out;
 }
 
+// Gradient of sum_px grad_out[px] * relaxed(px).  With target != NULL
+// (L2 fit), grad_out is 2 (image - target) of the pixel's own image value,
+// which is written to out_img, and the loss sum (image - target)^2 is
+// reduced as component ng.
 __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant__ KParams P, const FrameDesc F,
-                                                          const float* grad_out, float* out_relaxed,
+                                                          const float* grad_out, const float* target,
+                                                          float* out_img, float* out_relaxed,
                                                           double* partial, int ng) {
     __shared__ Tables T;
-    __shared__ double red[kBwdThreads / 32][kMaxGrad];
+    __shared__ double red[kBwdThreads / 32][kMaxGrad + 1];
     const int nwords = (int)(sizeof(DfTables) / 4) + rot_entries(P.M) * (int)(sizeof(RotEntry) / 4);
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(&P.tables);
@@ -244,38 +257,56 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
         for (int k = threadIdx.x; k < nwords; k += blockDim.x) dst[k] = src[k];
     }
     __syncthreads();
-    double mine[kMaxGrad];
-    for (int k = 0; k < ng; ++k) mine[k] = 0.0;
+    const int nc = target ? ng + 1 : ng;          // components reduced
+    double mine[kMaxGrad + 1];
+    for (int k = 0; k < nc; ++k) mine[k] = 0.0;
     const int stride = gridDim.x * blockDim.x;
     for (int px = blockIdx.x * blockDim.x + threadIdx.x; px < F.npx; px += stride) {
-        const float o = pixel_grad(P, T, F, px, (double)grad_out[px], mine);
+        float g[kMaxGrad], disc;
+        const float o = pixel_grad(P, T, F, px, g, ng, &disc);
         if (out_relaxed) out_relaxed[px] = o;
+        double go;
+        if (target) {
+            const float r = disc - target[px];
+            out_img[px] = disc;
+            go = 2.0 * (double)r;
+            mine[ng] += (double)r * (double)r;
+        } else {
+            go = (double)grad_out[px];
+        }
+        if (go != 0.0)
+            for (int k = 0; k < ng; ++k) mine[k] += go * (double)g[k];
     }
     // fixed-order reduction over the CTA: a shuffle tree per warp, then the
     // warps' sums in warp order
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int k = 0; k < ng; ++k) {
+    for (int k = 0; k < nc; ++k) {
         double v = mine[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) red[w][k] = v;
     }
     __syncthreads();
-    if ((int)threadIdx.x < ng) {
+    if ((int)threadIdx.x < nc) {
         double t = 0.0;
         for (int ww = 0; ww < kBwdThreads / 32; ++ww) t += red[ww][threadIdx.x];
-        partial[(size_t)blockIdx.x * ng + threadIdx.x] = t;
+        partial[(size_t)blockIdx.x * nc + threadIdx.x] = t;
     }
 }
 
-// grad[k] = sum over the CTA partials: warp k sums blocks lane, lane + 32,
-// ... in order, then a shuffle tree; a fixed order, so deterministic.
-__global__ void bwd_reduce_kernel(const double* partial, int nblocks, int ng, float* grad) {
+// Sum over the CTA partials of nc components: warp k sums blocks lane,
+// lane + 32, ... in order, then a shuffle tree; a fixed order, so
+// deterministic.  Components 0..ng-1 go to grad, component ng (if nc > ng)
+// to *loss.
+__global__ void bwd_reduce_kernel(const double* partial, int nblocks, int nc, int ng, float* grad, float* loss) {
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (k >= ng) return;
+    if (k >= nc) return;
     double s = 0.0;
-    for (int b = lane; b < nblocks; b += 32) s += partial[(size_t)b * ng + k];
+    for (int b = lane; b < nblocks; b += 32) s += partial[(size_t)b * nc + k];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) grad[k] = (float)s;
+    if (lane == 0) {
+        if (k < ng) grad[k] = (float)s;
+        else if (loss) *loss = (float)s;
+    }
 }
 
 // One pixel per thread up to 8 CTAs per SM, then a grid-stride loop.
@@ -295,32 +326,62 @@ extern "C" {
 size_t glint_backward_workspace_size(const GlintFrame* frame) {
     if (!frame || frame->width <= 0 || frame->height <= 0 || frame->n_lights < 0 || frame->n_lights > GLINT_MAX_LIGHTS)
         return 0;
-    const int ng = 3 + 3 * frame->n_lights;
-    return (size_t)bwd_blocks(frame->width * frame->height) * ng * sizeof(double);
+    const int nc = 4 + 3 * frame->n_lights;           // the gradient and the L2 loss
+    return (size_t)bwd_blocks(frame->width * frame->height) * nc * sizeof(double);
 }
 
-int glint_backward(const GlintFrame* frame, const GlintMaterial* material, const GlintLight* lights,
-                   const float* grad_out, float* grad, float* out_relaxed, void* workspace, size_t ws_bytes,
-                   void* stream) {
+}  // extern "C"
+
+namespace {
+
+// Shared by glint_backward (grad_out given) and glint_fit_l2 (target given).
+int launch_backward(const GlintFrame* frame, const GlintMaterial* material, const GlintLight* lights,
+                    const float* grad_out, const float* target, float* out_img, float* grad, float* loss,
+                    float* out_relaxed, void* workspace, size_t ws_bytes, void* stream) {
     int rc = check_frame_shape(frame, lights);
     if (rc) return rc;
     if (frame->mat_px) return GLINT_ERR_UNSUPPORTED;            // gradients of the scalar material only
     KParams P;
     if ((rc = make_material_params(material, lights, frame->n_lights, &P))) return rc;
     if ((rc = check_frame_device(frame, lights))) return rc;
-    if ((rc = check_device_ptr(grad_out, 4)) || (rc = check_device_ptr(grad, 4))) return rc;
+    if (grad_out && (rc = check_device_ptr(grad_out, 4))) return rc;
+    if (target && ((rc = check_device_ptr(target, 4)) || (rc = check_device_ptr(out_img, 4)))) return rc;
+    if ((rc = check_device_ptr(grad, 4))) return rc;
+    if (loss && (rc = check_device_ptr(loss, 4))) return rc;
     if (out_relaxed && (rc = check_device_ptr(out_relaxed, 4))) return rc;
     const size_t need = glint_backward_workspace_size(frame);
     if (!workspace || ws_bytes < need) return GLINT_ERR_WORKSPACE;
     if ((rc = check_device_ptr(workspace, 8))) return rc;
     const FrameDesc F = make_frame_desc(frame, nullptr);
     const int ng = 3 + 3 * frame->n_lights;
+    const int nc = target ? ng + 1 : ng;
     const int blocks = bwd_blocks(F.npx);
     cudaStream_t s = (cudaStream_t)stream;
-    bwd_kernel<<<blocks, kBwdThreads, 0, s>>>(P, F, grad_out, out_relaxed, static_cast<double*>(workspace), ng);
+    bwd_kernel<<<blocks, kBwdThreads, 0, s>>>(P, F, grad_out, target, out_img, out_relaxed,
+                                              static_cast<double*>(workspace), ng);
     if ((rc = cuda_rc(cudaGetLastError()))) return rc;
-    bwd_reduce_kernel<<<1, 32 * ng, 0, s>>>(static_cast<const double*>(workspace), blocks, ng, grad);
+    bwd_reduce_kernel<<<1, 32 * nc, 0, s>>>(static_cast<const double*>(workspace), blocks, nc, ng, grad, loss);
     return cuda_rc(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+int glint_backward(const GlintFrame* frame, const GlintMaterial* material, const GlintLight* lights,
+                   const float* grad_out, float* grad, float* out_relaxed, void* workspace, size_t ws_bytes,
+                   void* stream) {
+    if (!grad_out) return GLINT_ERR_ARG;
+    return launch_backward(frame, material, lights, grad_out, nullptr, nullptr, grad, nullptr, out_relaxed,
+                           workspace, ws_bytes, stream);
+}
+
+int glint_fit_l2(const GlintFrame* frame, const GlintMaterial* material, const GlintLight* lights,
+                 const float* target, float* out, float* grad, float* loss, void* workspace, size_t ws_bytes,
+                 void* stream) {
+    if (!target || !out) return GLINT_ERR_ARG;
+    return launch_backward(frame, material, lights, nullptr, target, out, grad, loss, nullptr, workspace,
+                           ws_bytes, stream);
 }
 
 }  // extern "C"

@@ -215,6 +215,34 @@ def backward(scene: Scene, grad_out: torch.Tensor, material=None, lights=None, r
     return (grad, rel) if (relaxed or out_relaxed is not None) else grad
 
 
+def fit_l2(scene: Scene, target: torch.Tensor, material=None, lights=None, stream=None, workspace=None,
+           out=None, grad=None, loss=None):
+    """glint_fit_l2: one pass giving the image (out), the L2 loss
+    sum((out - target)^2) and its gradient with respect to (alpha_x,
+    alpha_y, ln_density, light directions), through the relaxed counts.
+    Returns (out, grad, loss) as device tensors."""
+    material = material or scene.material
+    lights = scene.lights if lights is None else lights
+    dev = scene.gbuf.device
+    H, W = scene.height, scene.width
+    _check_plane(target, "target", (H, W), dev)
+    frame = _lib.frame_struct(scene.gbuf, scene.light_px, scene.mat_px, len(lights))
+    nbytes = int(_lib.lib().glint_backward_workspace_size(C.byref(frame)))
+    ws = workspace if workspace is not None else torch.empty(max(nbytes, 8) // 8 + 1, dtype=torch.float64, device=dev)
+    out = out if out is not None else torch.empty(H, W, dtype=torch.float32, device=dev)
+    _check_plane(out, "out", (H, W), dev)
+    grad = grad if grad is not None else torch.empty(3 + 3 * len(lights), dtype=torch.float32, device=dev)
+    loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=dev)
+    mat = _lib.material_struct(material)
+    lts = _lib.lights_struct(lights)
+    with torch.cuda.device(dev):
+        rc = _lib.lib().glint_fit_l2(C.byref(frame), C.byref(mat), lts, target.data_ptr(), out.data_ptr(),
+                                     grad.data_ptr(), loss.data_ptr(), ws.data_ptr(), ws.numel() * 8,
+                                     _stream_handle(stream))
+    _lib.check(rc, "glint_fit_l2")
+    return out, grad, loss
+
+
 class GlintBRDF(torch.autograd.Function):
     """Glint image as a differentiable function of the scalar material
     roughness, ln flake density and the directions of directional lights.

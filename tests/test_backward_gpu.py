@@ -142,3 +142,56 @@ def test_backward_argument_errors(fit):
     go2 = torch.zeros(rnd.height, rnd.width, device=DEV)
     assert L.glint_backward(C.byref(fr2), C.byref(mat), _lib.lights_struct(rnd.lights), go2.data_ptr(),
                             torch.empty(9, device=DEV).data_ptr(), None, ws.data_ptr(), 16 * 8, None) == -5
+
+
+def test_fit_l2_one_pass_matches_forward_plus_backward(orc, fit):
+    """glint_fit_l2: image equal to glint_eval's up to summation order, loss
+    and gradient equal to render -> 2 (img - target) -> glint_backward, and
+    the gradient equal to the oracle's for the same grad_out."""
+    sc, scd, go = fit
+    tgt = scenes.plane_sphere_fit(target=True)
+    timg = glint.render_scene(scd, material=tgt.material, lights=tgt.lights)
+    img = glint.render_scene(scd)
+    out, g, loss = glint.fit_l2(scd, timg)
+    torch.cuda.synchronize()
+    a, b = out.double(), img.double()
+    scale = b.abs().mean().item()
+    assert ((a - b).abs() / b.abs().clamp_min(1e-6 * scale)).max().item() <= 1e-5
+    ref_loss = ((img.double() - timg.double()) ** 2).sum().item()
+    assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss
+    g2 = glint.backward(scd, (2.0 * (img - timg)).contiguous())
+    gg, gr = g.double().cpu().numpy(), g2.double().cpu().numpy()
+    for k in range(6):
+        assert abs(gg[k] - gr[k]) <= 1e-4 * abs(gr[k]) + 1e-7 * np.abs(gr).max(), (NAMES[k], gg[k], gr[k])
+    go_fused = (2.0 * (out.double() - timg.double())).cpu().numpy().reshape(-1)
+    g6, _, _ = orc.grad(sc, go_fused)
+    for k in range(6):
+        assert abs(gg[k] - g6[k]) <= 1e-3 * abs(g6[k]) + 1e-6 * np.abs(g6).max(), (NAMES[k], gg[k], g6[k])
+
+
+def test_fit_l2_repeatable_and_argument_errors(fit):
+    sc, scd, go = fit
+    import ctypes as C
+    tgt = torch.zeros(sc.height, sc.width, device=DEV)
+    o1, g1, l1 = glint.fit_l2(scd, tgt)
+    o2, g2, l2 = glint.fit_l2(scd, tgt)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o2) and torch.equal(g1, g2) and torch.equal(l1, l2)
+    L = _lib.lib()
+    frame = _lib.frame_struct(scd.gbuf, None, None, 1)
+    mat = _lib.material_struct(sc.material)
+    lts = _lib.lights_struct(sc.lights)
+    ws = torch.empty(16, dtype=torch.float64, device=DEV)
+    out = torch.empty_like(tgt)
+    g = torch.empty(6, device=DEV)
+    assert L.glint_fit_l2(C.byref(frame), C.byref(mat), lts, None, out.data_ptr(), g.data_ptr(), None,
+                          ws.data_ptr(), 16 * 8, None) == -1
+    assert L.glint_fit_l2(C.byref(frame), C.byref(mat), lts, tgt.data_ptr(), out.data_ptr(), g.data_ptr(), None,
+                          ws.data_ptr(), 16 * 8, None) == -6
+    rnd = scenes.random_gbuffer(seed=1).to(DEV)
+    fr2 = _lib.frame_struct(rnd.gbuf, rnd.light_px, rnd.mat_px, len(rnd.lights))
+    t2 = torch.zeros(rnd.height, rnd.width, device=DEV)
+    o3 = torch.empty_like(t2)
+    assert L.glint_fit_l2(C.byref(fr2), C.byref(mat), _lib.lights_struct(rnd.lights), t2.data_ptr(),
+                          o3.data_ptr(), torch.empty(9, device=DEV).data_ptr(), None, ws.data_ptr(), 16 * 8,
+                          None) == -5
