@@ -335,6 +335,15 @@ struct Cell { GridVert v[3]; double lam[3]; int tri; int m; double x, t; };
 
 Cell ratio_cell(double rho_r, double phi, int M) {
     Cell c;
+    if (M == 0) {
+        /* Isotropic grids only (Sec. 4 without Sec. 5): the single grid of
+         * ring 0 carries the whole weight; the footprint's anisotropy was
+         * handled by the split into pieces along the major axis. */
+        c.m = 0; c.x = 0.0; c.t = 0.0; c.tri = 0;
+        for (int k = 0; k < 3; ++k) c.v[k] = {0, 0};
+        c.lam[0] = 1.0; c.lam[1] = 0.0; c.lam[2] = 0.0;
+        return c;
+    }
     const double rr = std::min(std::max(rho_r, 0.0), (double)M);
     const int m = std::min((int)std::floor(rr), M - 1);
     const double x = rr - m;
@@ -498,6 +507,14 @@ T gated_count(const CountLaw<T>& L, double th0, double th1, bool relaxed,
     return cc;
 }
 
+/* Isotropic-grid mode (M = 0, Sec. 4 with manual anisotropic filtering): the
+ * tetrahedron degenerates to the segment between the two LODs of the single
+ * isotropic grid - vertex 0 (lower LOD, weight 1 - s) and vertex 3 (upper LOD,
+ * weight s), the distributed binomial of Sec. 4.2 - and the two zero-weight
+ * vertices 1, 2 are not evaluated: 2 x 3 x 4 = 24 evaluations per piece and
+ * light instead of 48. */
+static bool vertex_used(int M, int i) { return M > 0 || i == 0 || i == 3; }
+
 /* ------------------------------------------------------------------------ */
 /* Full pixel evaluation (Steps 1-10 in order).                              */
 /* ------------------------------------------------------------------------ */
@@ -593,6 +610,7 @@ T eval_pixel(const Scene& sc, int px, const Seeds& sd, bool relaxed, Trace* tr) 
         TetVert<T> tv[4];
         S.tet = tet_split(S.cell.lam, S.lod.s, tv);
         for (int i = 0; i < 4; ++i) {
+            if (!vertex_used(M.n_rings, i)) continue;
             VertData& V = S.vd[i];
             V.upper = tv[i].upper;
             V.level = S.lod.level + tv[i].upper;
@@ -661,6 +679,7 @@ T eval_pixel(const Scene& sc, int px, const Seeds& sd, bool relaxed, Trace* tr) 
         for (int sub = 0; sub < sp.K; ++sub) {
             const SubData& S = subs[sub];
             for (int i = 0; i < 4; ++i) {
+                if (!vertex_used(M.n_rings, i)) continue;
                 const VertData& V = S.vd[i];
                 const CountLaw<T> law = count_law(V.n, p);
                 for (int j = 0; j < 3; ++j) {
@@ -716,7 +735,7 @@ int check_material(const OMaterial* m, int nL) {
     if (!m) return -1;
     if (m->ndf != 0 && m->ndf != 1) return -1;
     if (m->n_lods < 2 || m->n_lods > 16) return -1;
-    if (m->n_rings < 1 || m->n_rings > 6) return -1;
+    if (m->n_rings < 0 || m->n_rings > 6) return -1;
     if (m->lod_factor != 2 && m->lod_factor != 4) return -1;
     if (m->max_sub < 1 || m->max_sub > 64) return -1;
     if (!(m->R > 0.0f && m->R <= 1.0f) || !(m->gamma >= 1e-3f)) return -1;
