@@ -37,6 +37,7 @@ WORKLOAD = "sphere_plane 3840x2160, 2 point lights, per-pixel alpha U[0.05,0.5] 
 # minimal FP32 / INT32 operations of each step (see the design notes):
 OPS_PER_PIXEL = 120        # frame, footprint SVD / atan2 / log2, split
 OPS_PER_SUB = 350          # LOD, cell, tetrahedron, 4 grid transforms + simplex, 12 spatial hashes
+OPS_PER_SUB_ISO = 200      # the same with 2 grid vertices (isotropic-grid mode)
 OPS_PER_PIXEL_LIGHT = 180  # half-vector, NDF ratio, angular texels + 4 hashes, Fresnel, Smith, shade
 OPS_PER_SUB_LIGHT = 60     # 4 gated-binomial parameter sets (P>=1, mu, sigma, ceil n)
 OPS_PER_EVAL = 11          # one hash word (combine + fmix32) and the gate test
@@ -134,22 +135,27 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def census(glint, scene_dev):
+def census(glint, scene_dev, material=None):
     """Exact work counts of one frame: pixels shaded, sub-footprints,
     pixel-lights, evaluations (trace kernel with no record capacity)."""
+    material = material or scene_dev.material
+    per = 24 if material.n_rings == 0 else 48          # evaluations per sub-footprint and light
     n = scene_dev.width * scene_dev.height
     tot = dict(px=0, sub=0, pl=0, sl=0, evals=0)
     chunk = 1 << 21
     for s in range(0, n, chunk):
-        pix, _ = glint.trace(scene_dev, np.arange(s, min(n, s + chunk), dtype=np.int32), cap=0)
+        pix, _ = glint.trace(scene_dev, np.arange(s, min(n, s + chunk), dtype=np.int32), cap=0, material=material)
         ok = pix["status"] == 0
         K = pix["K"][ok].astype(np.int64)
         nrec = pix["n_rec"][ok].astype(np.int64)
-        lights_on = np.where(K > 0, nrec // (48 * np.maximum(K, 1)), 0)
+        lights_on = np.where(K > 0, nrec // (per * np.maximum(K, 1)), 0)
         tot["px"] += int(ok.sum()); tot["sub"] += int(K.sum()); tot["pl"] += int(lights_on.sum())
         tot["sl"] += int((K * lights_on).sum()); tot["evals"] += int(nrec.sum())
-    tot["ops"] = (OPS_PER_PIXEL * tot["px"] + OPS_PER_SUB * tot["sub"] + OPS_PER_PIXEL_LIGHT * tot["pl"]
-                  + OPS_PER_SUB_LIGHT * tot["sl"] + OPS_PER_EVAL * tot["evals"])
+    # isotropic-grid mode: 2 grid vertices instead of 4 (2 grid transforms and
+    # 6 spatial hashes per sub-footprint, 2 count laws per sub-footprint-light)
+    o_sub, o_sl = (OPS_PER_SUB, OPS_PER_SUB_LIGHT) if per == 48 else (OPS_PER_SUB_ISO, OPS_PER_SUB_LIGHT // 2)
+    tot["ops"] = (OPS_PER_PIXEL * tot["px"] + o_sub * tot["sub"] + OPS_PER_PIXEL_LIGHT * tot["pl"]
+                  + o_sl * tot["sl"] + OPS_PER_EVAL * tot["evals"])
     return tot
 
 
@@ -352,6 +358,42 @@ def run_fwd_bwd(args, dev):
             "grad": [float(x) for x in grad.cpu()]}
 
 
+def run_isotropic(args, dev):
+    """Sec. 4 with hand-filtered anisotropy (n_rings = 0: the footprint cut
+    into ceil(r) pieces on the isotropic grid) against the anisotropic grids
+    of Sec. 5, on the 1920x1080 grazing plane whose far rows reach 32:1."""
+    import dataclasses
+    from paper_2306_05051_gb300 import glint, scenes
+    sc = scenes.grazing_plane(device=dev)
+    out = torch.empty(sc.height, sc.width, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    res = {}
+    # with 16 LODs no footprint of this plane exceeds the top level, so only
+    # the anisotropy cuts footprints
+    m16 = dataclasses.replace(sc.material, n_lods=16)
+    for name, m in (("anisotropic_grids", sc.material), ("isotropic_grids", dataclasses.replace(sc.material, n_rings=0)),
+                    ("anisotropic_grids_16_lods", m16), ("isotropic_grids_16_lods", dataclasses.replace(m16, n_rings=0))):
+        for _ in range(args.warmup):
+            glint.render_scene(sc, out=out, stream=stream, material=m)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = max(3, min(args.steps, 50))
+        stream.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            glint.render_scene(sc, out=out, stream=stream, material=m)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        cen = census(glint, sc, material=m)
+        res[name] = {"ms": ms, "gpixel_s": sc.width * sc.height / (ms * 1e-3) / 1e9, "evals": cen["evals"],
+                     "sub_footprints": cen["sub"], "roofline": roofline_of(cen["ops"], ms)}
+    res["workload"] = "grazing_plane 1920x1080, directional light, anisotropy to 32:1 (C2)"
+    res["isotropic_over_anisotropic_time"] = res["isotropic_grids"]["ms"] / res["anisotropic_grids"]["ms"]
+    res["isotropic_over_anisotropic_time_16_lods"] = (res["isotropic_grids_16_lods"]["ms"]
+                                                      / res["anisotropic_grids_16_lods"]["ms"])
+    return res
+
+
 def cpu_baseline(seconds=12.0, sc=None):
     """The FP64 oracle on the host cores on a deterministic row sample of the
     same 4K frame (every 64th row, then further rows until ~seconds)."""
@@ -385,6 +427,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fwd-bwd", action="store_true")
+    ap.add_argument("--no-isotropic", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -455,6 +498,8 @@ def main():
         line["batched"] = run_batched(args, dev)
     if not args.no_fwd_bwd:
         line["fwd_bwd"] = run_fwd_bwd(args, dev)
+    if not args.no_isotropic:
+        line["isotropic_grids"] = run_isotropic(args, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -57,7 +57,7 @@ int check_material(const GlintMaterial* m) {
     if (!m) return GLINT_ERR_ARG;
     if (m->ndf != 0 && m->ndf != 1) return GLINT_ERR_ARG;
     if (m->n_lods < 2 || m->n_lods > GLINT_MAX_LODS) return GLINT_ERR_ARG;
-    if (m->n_rings < 1 || m->n_rings > GLINT_MAX_RINGS) return GLINT_ERR_ARG;
+    if (m->n_rings < 0 || m->n_rings > GLINT_MAX_RINGS) return GLINT_ERR_ARG;
     if (m->lod_factor != 2 && m->lod_factor != 4) return GLINT_ERR_ARG;
     if (m->max_sub < 1 || m->max_sub > GLINT_MAX_SUB) return GLINT_ERR_ARG;
     if (!(m->R > 0.0f && m->R <= 1.0f) || !(m->gamma >= 1e-3f) || !std::isfinite(m->gamma)) return GLINT_ERR_ARG;

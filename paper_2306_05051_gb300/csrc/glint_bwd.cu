@@ -172,6 +172,7 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
                 return 0.0f;
             }
             for (int i = 0; i < 4; ++i) {
+                if (!vertex_used(P.M, i)) continue;
                 float X[3];
                 for (int j = 0; j < 3; ++j) {
                     float ct[4];

@@ -110,6 +110,7 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
             if (!__any_sync(0xffffffffu, L.on)) continue;
 #pragma unroll 1
             for (int i = 0; i < 4; ++i) {
+                if (!vertex_used(P.M, i)) continue;
                 CountLaw law = count_law(S.ntr[i], L.p, L.lq);
                 if (!L.on) law.Tg = 0u;
 #pragma unroll
@@ -244,6 +245,7 @@ __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& 
             const LightState& L = ls[l];
             if (!L.on) continue;
             for (int i = 0; i < 4; ++i) {
+                if (!vertex_used(P.M, i)) continue;
                 const CountLaw law = count_law(S.ntr[i], L.p, L.lq);
                 for (int j = 0; j < 3; ++j) {
                     for (int k = 0; k < 4; ++k) {

@@ -153,6 +153,12 @@ __device__ __forceinline__ float smith_lambda(int ndf, float ax, float ay, float
     return 0.5f * (sqrtf(1.0f + 1.0f / (a * a)) - 1.0f);
 }
 
+// Isotropic-grid mode (M = 0: Sec. 4 with the anisotropic footprint cut into
+// pieces along its major axis, no Sec. 5 rings): the tetrahedron degenerates
+// to the two LODs of the isotropic grid, vertex 0 (weight 1 - s) and vertex 3
+// (weight s); vertices 1 and 2 have weight 0 and are not evaluated.
+__host__ __device__ __forceinline__ bool vertex_used(int M, int i) { return M > 0 || i == 0 || i == 3; }
+
 struct Vert {           // one tetrahedron vertex (a virtual grid)
     int ring, kor, level;
 };
@@ -315,7 +321,7 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
     if (!dflt(rr, (float)P.M)) rr = mkdf((float)P.M);
     df fx_unused;
     int m = dffloor(rr, &fx_unused);
-    if (m > P.M - 1) m = P.M - 1;
+    if (P.M > 0 && m > P.M - 1) m = P.M - 1;
     const df x = rr - (float)m;
     const int nm = m == 0 ? 4 : (1 << (m + 1));
     df t;
@@ -325,7 +331,12 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
     // arrays, so nothing below is indexed at run time
     int r0, k0, r1, k1, r2, k2;
     df lam0, lam1, lam2;
-    if (m == 0) {
+    if (P.M == 0) {
+        // isotropic grids only (Sec. 4): ring 0 carries the whole weight
+        r0 = k0 = r1 = k1 = r2 = k2 = 0;
+        lam0 = mkdf(1.0f);
+        lam1 = lam2 = mkdf(0.0f);
+    } else if (m == 0) {
         r0 = 0; k0 = 0; r1 = 1; k1 = a; r2 = 1; k2 = (a + 1) & 3;
         lam0 = 1.0f - x;
         lam1 = x * (1.0f - t);
@@ -486,6 +497,7 @@ static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T,
     }
 #pragma unroll 1
     for (int i = 0; i < 4; ++i) {
+        if (!vertex_used(P.M, i)) continue;
         const Vert V = S.vert[i];
         U.gid[i] = ((uint32_t)V.level << 16) | ((uint32_t)V.ring << 8) | (uint32_t)V.kor;
         const RotEntry Q = T.rot[rot_index(V.ring, V.kor)];

@@ -217,3 +217,40 @@ def test_every_launch_shape_gives_the_same_bits():
         with pytest.raises(_lib.GlintError) as e:
             glint.render_scene(scd, launch=bad)
         assert e.value.code == -1, bad
+
+
+def _iso(sc):
+    import dataclasses
+    return dataclasses.replace(sc, material=dataclasses.replace(sc.material, n_rings=0))
+
+
+@pytest.mark.parametrize("which", ["grazing_plane", "plane45", "random"])
+def test_isotropic_grid_mode(orc, which):
+    """n_rings = 0 (Sec. 4 with the footprint cut into ceil(r) pieces on the
+    isotropic grid): parity with the oracle, 24 evaluations per piece and
+    light, and K growing with the anisotropy."""
+    if which == "grazing_plane":
+        sc = _iso(scenes.grazing_plane())
+    elif which == "plane45":
+        sc = _iso(scenes.plane45())
+    else:
+        sc = _iso(scenes.random_gbuffer(seed=4))
+    scd = sc.to(DEV)
+    img = _render(scd)
+    if which == "grazing_plane":
+        rng = np.random.default_rng(8)
+        fg = np.flatnonzero(sc.gbuf[..., 6:9].abs().sum(-1).reshape(-1).numpy() > 0)
+        px = np.unique(rng.choice(fg, 12000, replace=False)).astype(np.int32)
+        ref = orc.eval_image(sc, px=px)
+        s = parity.check_image(orc, sc, scd, img, ref, px=px, sample_trace=300)
+    else:
+        ref = orc.eval_image(sc)
+        s = parity.check_image(orc, sc, scd, img, ref, sample_trace=300)
+        px = np.arange(img.size, dtype=np.int32)
+    _summary(f"isotropic grids {which}", s)
+    pix, _ = glint.trace(scd, px[:4000], cap=0)
+    ok = pix["status"] == 0
+    nl_on = pix["n_rec"][ok] // np.maximum(24 * pix["K"][ok], 1)
+    assert (pix["n_rec"][ok] == 24 * pix["K"][ok] * nl_on).all()
+    if which == "grazing_plane":
+        assert pix["K"][ok].max() >= 8                     # far rows: anisotropy cut into many pieces
