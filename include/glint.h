@@ -61,8 +61,12 @@ extern "C" {
  *               (Sec. 5.2, "subdivide it to account for the glints'
  *               micro-roughness").
  *   n_lods      L, 2..16 levels of detail; level l holds f^l flakes per texel.
- *   n_rings     M, 1..6 anisotropy rings; ring m has ratio 2^m and 2^(m+1)
- *               orientations (Fig. 5).
+ *   n_rings     M, 0..6 anisotropy rings; ring m has ratio 2^m and 2^(m+1)
+ *               orientations (Fig. 5).  M = 0: isotropic grids only, the
+ *               Sec. 4 method with the anisotropy filtered by hand - the
+ *               footprint is cut along its major axis into ceil(r) pieces,
+ *               each evaluated at its two LODs (24 evaluations per piece and
+ *               light instead of 48).
  *   lod_factor  f, area ratio between consecutive LODs: 2 or 4 (Eq. 13 writes
  *               powers of two; Sec. 1 says consecutive LODs quadruple).
  *   max_sub     K_max, 1..64: most sub-footprints one pixel is cut into when
