@@ -167,7 +167,9 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
             // the sub-footprints are the same for every light, so a
             // coordinate out of range shows at the first light that is on,
             // before this pixel has added anything to mine[]
-            if (!setup_sub<true>(P, T, S, sub, U, U.S0, U.uw, 1)) {
+            const bool ok = P.M > 0 ? setup_sub<true, false>(P, T, S, sub, U, U.S0, U.uw, 1)
+                                    : setup_sub<true, true>(P, T, S, sub, U, U.S0, U.uw, 1);
+            if (!ok) {
                 for (int k = 0; k < ng; ++k) g[k] = 0.0f;
                 return 0.0f;
             }

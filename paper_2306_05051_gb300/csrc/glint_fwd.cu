@@ -71,6 +71,8 @@ struct LightEval {          // what the evaluation loop needs of one light
 
 // Shade the pixel of this lane (px valid or not); all 32 lanes call together.
 // ss0 / suw: the CTA's shared arrays of 12 x blockDim spatial words / weights.
+// kIso: isotropic-grid mode (M = 0), tetrahedron vertices 0 and 3 only.
+template <bool kIso>
 __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& F, WarpQueue& q, int px,
                             bool valid, uint32_t* ss0, float* suw) {
     const int lane = threadIdx.x & 31;
@@ -97,7 +99,7 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
         SubState U;
         bool act = sub < K && in_range;
         if (act) {
-            in_range = setup_sub<false>(P, T, S, sub, U, s0s, uws, st);
+            in_range = setup_sub<false, kIso>(P, T, S, sub, U, s0s, uws, st);
             act = in_range;
         }
 #pragma unroll 1
@@ -109,8 +111,8 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
             for (int k = 0; k < 4; ++k) { L.v[k] = ls[l].v[k]; L.A0[k] = ls[l].A0[k]; L.A1[k] = ls[l].A1[k]; }
             if (!__any_sync(0xffffffffu, L.on)) continue;
 #pragma unroll 1
-            for (int i = 0; i < 4; ++i) {
-                if (!vertex_used(P.M, i)) continue;
+            for (int ii = 0; ii < (kIso ? 2 : 4); ++ii) {
+                const int i = kIso ? 3 * ii : ii;
                 CountLaw law = count_law(S.ntr[i], L.p, L.lq);
                 if (!L.on) law.Tg = 0u;
 #pragma unroll
@@ -166,6 +168,7 @@ __device__ __forceinline__ int tile_pixel() {
     return (ln >> 2) * (nw * 4) + w * 4 + (ln & 3);
 }
 
+template <bool kIso>
 __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KParams P, const FrameDesc F) {
     extern __shared__ __align__(16) unsigned char smem[];
     Tables& T = *reinterpret_cast<Tables*>(smem);
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KPara
     for (int base = blockIdx.x * blockDim.x; base < F.npx; base += gridDim.x * blockDim.x) {
         __syncthreads();
         const int px = base + tile_pixel();
-        const float o = shade_warp(P, T, F, q, px, px < F.npx, ss0, suw);
+        const float o = shade_warp<kIso>(P, T, F, q, px, px < F.npx, ss0, suw);
         if (px < F.npx) F.out[px] = o;
     }
 }
@@ -189,6 +192,7 @@ __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KPara
 // tile_base[f] <= t < tile_base[f+1].  Persistent: CTAs take tiles from a
 // global counter (reset to 0 before the launch).  Otherwise one CTA per tile
 // (CTA b shades tile b), scheduled by the hardware.
+template <bool kIso>
 __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KParams P,
                                                      const __grid_constant__ BatchDesc B) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KPa
         }
         const FrameDesc& F = B.frames[lo];
         const int px = (t - B.tile_base[lo]) * (int)blockDim.x + tile_pixel();
-        const float o = shade_warp(P, T, F, q, px, px < F.npx, ss0, suw);
+        const float o = shade_warp<kIso>(P, T, F, q, px, px < F.npx, ss0, suw);
         if (px < F.npx) F.out[px] = o;
     }
 }
@@ -240,7 +244,9 @@ __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& 
     int nrec = 0;
     for (int sub = 0; sub < S.K; ++sub) {
         SubState U;
-        if (!setup_sub<true>(P, T, S, sub, U, U.S0, U.uw, 1)) { pr->status = 3; pr->n_rec = nrec; return; }
+        const bool ok = P.M > 0 ? setup_sub<true, false>(P, T, S, sub, U, U.S0, U.uw, 1)
+                                : setup_sub<true, true>(P, T, S, sub, U, U.S0, U.uw, 1);
+        if (!ok) { pr->status = 3; pr->n_rec = nrec; return; }
         for (int l = 0; l < F.nL; ++l) {
             const LightState& L = ls[l];
             if (!L.on) continue;
@@ -301,10 +307,11 @@ static cudaError_t configure_smem() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (configured_for == dev) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fwd_smem_bytes(1024));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem_bytes(1024));
+    const int mx = (int)fwd_smem_bytes(1024);
+    cudaError_t e = cudaFuncSetAttribute(fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) configured_for = dev;
     return e;
 }
@@ -312,18 +319,22 @@ static cudaError_t configure_smem() {
 cudaError_t launch_fwd(const KParams& P, const FrameDesc& F, cudaStream_t s, FwdLaunch cfg) {
     const cudaError_t e = configure_smem();
     if (e != cudaSuccess) return e;
-    fwd_kernel<<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, F);
+    if (P.M == 0) fwd_kernel<true><<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, F);
+    else fwd_kernel<false><<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, F);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const KParams& P, const BatchDesc& B, cudaStream_t s, FwdLaunch cfg) {
     const cudaError_t e = configure_smem();
     if (e != cudaSuccess) return e;
-    batch_kernel<<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, B);
+    if (P.M == 0) batch_kernel<true><<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, B);
+    else batch_kernel<false><<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, B);
     return cudaGetLastError();
 }
 
-const void* batch_kernel_fn() { return reinterpret_cast<const void*>(&batch_kernel); }
+const void* batch_kernel_fn(bool iso) {
+    return iso ? reinterpret_cast<const void*>(&batch_kernel<true>) : reinterpret_cast<const void*>(&batch_kernel<false>);
+}
 
 cudaError_t launch_trace(const KParams& P, const FrameDesc& F, const int32_t* px, int32_t n_px,
                          GlintTracePix* pix, GlintTraceRec* recs, int32_t cap, cudaStream_t s) {

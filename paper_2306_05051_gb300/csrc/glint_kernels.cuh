@@ -38,7 +38,7 @@ int cuda_rc(cudaError_t e);
 
 cudaError_t launch_fwd(const KParams& P, const FrameDesc& F, cudaStream_t s, FwdLaunch cfg);
 cudaError_t launch_batch(const KParams& P, const BatchDesc& B, cudaStream_t s, FwdLaunch cfg);
-const void* batch_kernel_fn();
+const void* batch_kernel_fn(bool iso);      // the batch kernel for the isotropic-grid mode or not
 size_t fwd_smem_bytes(int threads);
 FwdLaunch default_fwd_launch(int npx);
 FwdLaunch make_fwd_launch(int npx, int threads, int ctas_per_sm);

@@ -158,6 +158,8 @@ __device__ __forceinline__ float smith_lambda(int ndf, float ax, float ay, float
 // to the two LODs of the isotropic grid, vertex 0 (weight 1 - s) and vertex 3
 // (weight s); vertices 1 and 2 have weight 0 and are not evaluated.
 __host__ __device__ __forceinline__ bool vertex_used(int M, int i) { return M > 0 || i == 0 || i == 3; }
+// step of a loop over the used vertices 0..3 (0, 1, 2, 3 or 0, 3)
+__host__ __device__ __forceinline__ int vertex_step(int M) { return M > 0 ? 1 : 3; }
 
 struct Vert {           // one tetrahedron vertex (a virtual grid)
     int ring, kor, level;
@@ -331,12 +333,9 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
     // arrays, so nothing below is indexed at run time
     int r0, k0, r1, k1, r2, k2;
     df lam0, lam1, lam2;
-    if (P.M == 0) {
-        // isotropic grids only (Sec. 4): ring 0 carries the whole weight
-        r0 = k0 = r1 = k1 = r2 = k2 = 0;
-        lam0 = mkdf(1.0f);
-        lam1 = lam2 = mkdf(0.0f);
-    } else if (m == 0) {
+    // (M = 0, isotropic grids: rr = x = 0 here, so ring 0 takes the whole
+    // weight and the ring-1 vertices get weight 0; they are not evaluated)
+    if (m == 0) {
         r0 = 0; k0 = 0; r1 = 1; k1 = a; r2 = 1; k2 = (a + 1) & 3;
         lam0 = 1.0f - x;
         lam1 = x * (1.0f - t);
@@ -481,7 +480,8 @@ struct SubState {
 // image kernels keep those two in shared memory; pass U.S0, U.uw and stride 1
 // to keep them in U).  kTrace: also record the lattice vertices and
 // coordinates (li, lj, qx, qy, lower) for the trace and adjoint kernels.
-template <bool kTrace>
+// kIso: isotropic-grid mode (M = 0), vertices 0 and 3 only.
+template <bool kTrace, bool kIso>
 static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T, const PixelSetup& S, int sub,
                                               SubState& U, uint32_t* s0, float* uwo, int stride) {
     df us = S.u, vs = S.v;
@@ -496,8 +496,8 @@ static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T,
         vs = vs + (oa * S.u0y + ob * S.u0x);
     }
 #pragma unroll 1
-    for (int i = 0; i < 4; ++i) {
-        if (!vertex_used(P.M, i)) continue;
+    for (int ii = 0; ii < (kIso ? 2 : 4); ++ii) {
+        const int i = kIso ? 3 * ii : ii;
         const Vert V = S.vert[i];
         U.gid[i] = ((uint32_t)V.level << 16) | ((uint32_t)V.ring << 8) | (uint32_t)V.kor;
         const RotEntry Q = T.rot[rot_index(V.ring, V.kor)];

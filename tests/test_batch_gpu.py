@@ -98,3 +98,20 @@ def test_batch_argument_errors():
     for bad in [(100, 2), (512, -1), (512, 17)]:
         assert L.glint_ctx_set_launch(ctx._h, C.byref(_lib.GlintLaunch(*bad))) == -1
     ctx.close()
+
+
+def test_batch_switches_between_ring_and_isotropic_grids():
+    """One context, batches alternating n_rings = 4 and 0: each matches
+    glint_eval with that material bit for bit (the recorded graph follows
+    the kernel of the mode)."""
+    import dataclasses
+    fr = _frames(4)
+    m4 = fr[0].material
+    m0 = dataclasses.replace(m4, n_rings=0)
+    ctx = glint.BatchContext(DEV)
+    for m in (m4, m0, m4, m0):
+        outs = ctx.render(fr, material=m)
+        torch.cuda.synchronize()
+        for s, o in zip(fr, outs):
+            assert torch.equal(o, glint.render_scene(s, material=m))
+    ctx.close()
