@@ -282,13 +282,16 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
         if (dfsign(fr) > 0) c += 1;
         Kmaj = c >= P.Kmax ? P.Kmax : c;
     }
-    const df Ap = A_over(S.A, Kmaj);
+    // (for Kmaj == 1 and K == 1 the divisions and log2(Kmaj) = 0 are exact
+    // no-ops and are skipped)
+    const df Ap = Kmaj == 1 ? S.A : A_over(S.A, Kmaj);
     int ksub = 1;
     while (dflt(mkdf((float)(ksub * ksub) * P.top), Ap) && Kmaj * (ksub + 1) * (ksub + 1) <= P.Kmax) ++ksub;
     const int K = Kmaj * ksub * ksub;
     S.Kmaj = Kmaj; S.ksub = ksub; S.K = K;
-    const df As = A_over(S.A, K);
-    const df rho_r = dflog2(S.ratio, T.d) - dflog2(mkdf((float)Kmaj), T.d);
+    const df As = K == 1 ? S.A : A_over(S.A, K);
+    const df lr = dflog2(S.ratio, T.d);
+    const df rho_r = Kmaj == 1 ? lr : lr - dflog2(mkdf((float)Kmaj), T.d);
     if (K > 1) {
         // major axis u0 of the footprint (eigenvector of J J^T for sigma0^2),
         // oriented like (cos phi, sin phi) with phi in [0, pi)
