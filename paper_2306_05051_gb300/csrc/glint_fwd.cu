@@ -82,11 +82,14 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
     S.K = 0;
     if (valid) setup_pixel<false>(P, T, F, px, S);
     LightState ls[kMaxLights];
+    bool any_on = false;
     for (int l = 0; l < F.nL; ++l) {
         ls[l].on = false;
         if (S.status == 0) setup_light<false>(P, F, S, px, l, ls[l]);
+        any_on |= ls[l].on;
     }
-    const int K = S.status == 0 ? S.K : 0;
+    // a pixel that no light reaches shades to 0: its sub-footprints are not set up
+    const int K = S.status == 0 && any_on ? S.K : 0;
     const int Kw = __reduce_max_sync(0xffffffffu, K);
     float acc = 0.0f;
     int head = 0, count = 0;                     // warp-uniform queue state
