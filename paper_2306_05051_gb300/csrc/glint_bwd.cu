@@ -177,18 +177,29 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
                 if (!vertex_used(P.M, i)) continue;
                 float X[3];
                 for (int j = 0; j < 3; ++j) {
-                    float ct[4];
+                    // gates of the 4 texels first, then the open ones in texel order:
+                    // a warp runs the quantile as often as its busiest lane has open
+                    // gates, not once per texel that any lane opens
+                    unsigned om = 0u;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        om |= gate_open(fmix32(U.S0[3 * i + j] + L.A0[k]), law[i].Tg) ? (1u << k) : 0u;
+                    float ct[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                     float z0 = 0.0f, z1 = 0.0f, xd = 0.0f;
-                    for (int k = 0; k < 4; ++k) {
-                        ct[k] = 0.0f;
-                        const uint32_t h0 = fmix32(U.S0[3 * i + j] + L.A0[k]);
-                        if (gate_open(h0, law[i].Tg)) {
-                            const float z = normal_of_word(fmix32(U.S1[3 * i + j] + L.A1[k]));
-                            const float cc = 1.0f + law[i].mu + law[i].sig * z;
-                            ct[k] = fminf(fmaxf(cc, 1.0f), law[i].nceil);
-                            xd += L.v[k] * fminf(fmaxf(floorf(cc), 1.0f), law[i].nceil);
-                            if (cc > 1.0f && cc < law[i].nceil) { z0 += L.v[k]; z1 += L.v[k] * z; }
-                        }
+                    while (om) {
+                        const int k = __ffs(om) - 1;
+                        om &= om - 1u;
+                        const float vk = k == 0 ? L.v[0] : (k == 1 ? L.v[1] : (k == 2 ? L.v[2] : L.v[3]));
+                        const uint32_t a1 = k == 0 ? L.A1[0] : (k == 1 ? L.A1[1] : (k == 2 ? L.A1[2] : L.A1[3]));
+                        const float z = normal_of_word(fmix32(U.S1[3 * i + j] + a1));
+                        const float cc = 1.0f + law[i].mu + law[i].sig * z;
+                        const float ck = fminf(fmaxf(cc, 1.0f), law[i].nceil);
+                        ct[0] = k == 0 ? ck : ct[0];
+                        ct[1] = k == 1 ? ck : ct[1];
+                        ct[2] = k == 2 ? ck : ct[2];
+                        ct[3] = k == 3 ? ck : ct[3];
+                        xd += vk * fminf(fmaxf(floorf(cc), 1.0f), law[i].nceil);
+                        if (cc > 1.0f && cc < law[i].nceil) { z0 += vk; z1 += vk * z; }
                     }
                     X[j] = L.v[0] * ct[0] + L.v[1] * ct[1] + L.v[2] * ct[2] + L.v[3] * ct[3];
                     const float u = U.uw[3 * i + j];
