@@ -175,40 +175,40 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
             }
             for (int i = 0; i < 4; ++i) {
                 if (!vertex_used(P.M, i)) continue;
-                float X[3];
-                for (int j = 0; j < 3; ++j) {
-                    // gates of the 4 texels first, then the open ones in texel order:
-                    // a warp runs the quantile as often as its busiest lane has open
-                    // gates, not once per texel that any lane opens
-                    unsigned om = 0u;
+                // the 12 gates of this grid vertex first, then the open ones in
+                // (simplex vertex, texel) order
+                unsigned om = 0u;
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        om |= gate_open(fmix32(U.S0[3 * i + j] + L.A0[k]), law[i].Tg) ? (1u << k) : 0u;
-                    float ct[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                    float z0 = 0.0f, z1 = 0.0f, xd = 0.0f;
-                    while (om) {
-                        const int k = __ffs(om) - 1;
-                        om &= om - 1u;
-                        const float vk = k == 0 ? L.v[0] : (k == 1 ? L.v[1] : (k == 2 ? L.v[2] : L.v[3]));
-                        const uint32_t a1 = k == 0 ? L.A1[0] : (k == 1 ? L.A1[1] : (k == 2 ? L.A1[2] : L.A1[3]));
-                        const float z = normal_of_word(fmix32(U.S1[3 * i + j] + a1));
-                        const float cc = 1.0f + law[i].mu + law[i].sig * z;
-                        const float ck = fminf(fmaxf(cc, 1.0f), law[i].nceil);
-                        ct[0] = k == 0 ? ck : ct[0];
-                        ct[1] = k == 1 ? ck : ct[1];
-                        ct[2] = k == 2 ? ck : ct[2];
-                        ct[3] = k == 3 ? ck : ct[3];
-                        xd += vk * fminf(fmaxf(floorf(cc), 1.0f), law[i].nceil);
-                        if (cc > 1.0f && cc < law[i].nceil) { z0 += vk; z1 += vk * z; }
-                    }
-                    X[j] = L.v[0] * ct[0] + L.v[1] * ct[1] + L.v[2] * ct[2] + L.v[3] * ct[3];
-                    const float u = U.uw[3 * i + j];
-                    C += u * X[j];
-                    Cd += u * xd;
-                    Svx += u * ((1.0f - LG.fy) * (ct[1] - ct[0]) + LG.fy * (ct[3] - ct[2]));
-                    Svy += u * ((1.0f - LG.fx) * (ct[2] - ct[0]) + LG.fx * (ct[3] - ct[1]));
-                    Z0[i] += u * z0;
-                    Z1[i] += u * z1;
+                        om |= gate_open(fmix32(U.S0[3 * i + j] + L.A0[k]), law[i].Tg) ? (1u << (4 * j + k)) : 0u;
+                float X[3] = {0.0f, 0.0f, 0.0f};
+                const float u3[3] = {U.uw[3 * i], U.uw[3 * i + 1], U.uw[3 * i + 2]};
+                const uint32_t s13[3] = {U.S1[3 * i], U.S1[3 * i + 1], U.S1[3 * i + 2]};
+                const float fx = LG.fx, fy = LG.fy;
+                while (om) {
+                    const int b = __ffs(om) - 1;
+                    om &= om - 1u;
+                    const int j = b >> 2, k = b & 3;
+                    const float vk = k == 0 ? L.v[0] : (k == 1 ? L.v[1] : (k == 2 ? L.v[2] : L.v[3]));
+                    const uint32_t a1 = k == 0 ? L.A1[0] : (k == 1 ? L.A1[1] : (k == 2 ? L.A1[2] : L.A1[3]));
+                    const float uj = j == 0 ? u3[0] : (j == 1 ? u3[1] : u3[2]);
+                    const uint32_t s1 = j == 0 ? s13[0] : (j == 1 ? s13[1] : s13[2]);
+                    const float z = normal_of_word(fmix32(s1 + a1));
+                    const float cc = 1.0f + law[i].mu + law[i].sig * z;
+                    const float ck = fminf(fmaxf(cc, 1.0f), law[i].nceil);
+                    const float xk = vk * ck;
+                    X[0] += j == 0 ? xk : 0.0f;
+                    X[1] += j == 1 ? xk : 0.0f;
+                    X[2] += j == 2 ? xk : 0.0f;
+                    C += uj * xk;
+                    Cd += uj * vk * fminf(fmaxf(floorf(cc), 1.0f), law[i].nceil);
+                    const float axk = k == 0 ? -(1.0f - fy) : (k == 1 ? (1.0f - fy) : (k == 2 ? -fy : fy));
+                    const float ayk = k == 0 ? -(1.0f - fx) : (k == 1 ? -fx : (k == 2 ? (1.0f - fx) : fx));
+                    Svx += uj * axk * ck;
+                    Svy += uj * ayk * ck;
+                    if (cc > 1.0f && cc < law[i].nceil) { Z0[i] += uj * vk; Z1[i] += uj * vk * z; }
                 }
                 const float hx = 0.5f * U.qx[i], hy = 0.5f * U.qy[i];
                 Su += U.lower[i] ? hx * (X[1] - X[0]) + hy * (X[2] - X[1]) : hy * (X[1] - X[0]) + hx * (X[2] - X[1]);
