@@ -49,13 +49,16 @@ LANES_PER_SM = 128
 PROFILE = os.path.join(ROOT, "profiles", "fwd_kernel_sphere_plane_4k.md")
 
 
+FWD_SOURCES = ["glint_df.cuh", "glint_fwd.cu", "glint_kernels.cuh", "glint_pixel.cuh", "../../include/glint.h"]
+
+
 def kernel_source_hash():
-    """sha256 (first 16 hex digits) of the CUDA sources and the C header: a
-    DRAM-traffic figure taken from an ncu capture applies only while this is
-    unchanged."""
+    """sha256 (first 16 hex digits) of the sources the image kernel is built
+    from: a DRAM-traffic figure taken from an ncu capture of that kernel
+    applies only while this is unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_05051_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)) + ["../../include/glint.h"]:
+    for f in FWD_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
