@@ -148,7 +148,7 @@ int glint_eval_launch(const GlintFrame* frame, const GlintMaterial* material,
 /* The same evaluation with host buffers: copies every plane of `frame`
  * (host pointers, ideally pinned) into `staging` (device, caller-owned, at
  * least glint_eval_host_staging_size() bytes), evaluates, and copies the
- * image back to `out` (host).  The frame is processed in bands of about 1 M
+ * image back to `out` (host).  The frame is processed in bands of about 0.5 M
  * pixels of whole rows (at most 64 bands) so that copies in, kernels and
  * copies out of different bands overlap: the copies run on two internal
  * streams of the library (one pair per device, created on first use) that

@@ -222,7 +222,7 @@ int copy_streams(CopyStreams** out) {
     return GLINT_OK;
 }
 
-constexpr size_t kBandPixels = size_t(1) << 20;     // about 1 M pixels per band
+constexpr size_t kBandPixels = size_t(1) << 19;     // about 0.5 M pixels per band
 constexpr int kMaxBands = 64;
 
 // Copy in, shade and copy out a frame in bands of rows, so that the

@@ -152,9 +152,9 @@ def test_host_buffer_path_in_bands_matches_device_path(which):
     light and material planes: the banded, overlapped host path gives the
     device path's bits, and the stream it was given is ordered after it."""
     if which == "sphere_plane_tall":
-        sc = scenes.sphere_plane(1280, 2000, seed=11)          # 3 bands: 820, 820, 360 rows
+        sc = scenes.sphere_plane(1280, 2000, seed=11)          # 5 bands: 4 x 410 rows and 360
     else:
-        sc = scenes.grazing_plane()                           # 1920 x 1080, directional light, 2 bands
+        sc = scenes.grazing_plane()                           # 1920 x 1080, directional light, 4 bands
     scd = sc.to(DEV)
     dev_img = glint.render_scene(scd).cpu()
     pin = lambda t: None if t is None else t.pin_memory()
