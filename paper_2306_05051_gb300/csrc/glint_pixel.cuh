@@ -158,8 +158,6 @@ __device__ __forceinline__ float smith_lambda(int ndf, float ax, float ay, float
 // to the two LODs of the isotropic grid, vertex 0 (weight 1 - s) and vertex 3
 // (weight s); vertices 1 and 2 have weight 0 and are not evaluated.
 __host__ __device__ __forceinline__ bool vertex_used(int M, int i) { return M > 0 || i == 0 || i == 3; }
-// step of a loop over the used vertices 0..3 (0, 1, 2, 3 or 0, 3)
-__host__ __device__ __forceinline__ int vertex_step(int M) { return M > 0 ? 1 : 3; }
 
 struct Vert {           // one tetrahedron vertex (a virtual grid)
     int ring, kor, level;
