@@ -163,11 +163,13 @@ int glint_eval_host(const GlintFrame* host_frame, const GlintMaterial* material,
 
 /* Batched evaluation: many frames (each with its own planes, size and
  * n_lights; one material and one light array for all) shaded by ONE
- * persistent kernel whose CTAs take 1-tile work items from a counter, so
- * frames of uneven size and cost balance across the GPU.  The launch is
- * recorded in a CUDA graph (counter reset + kernel) owned by the context and
- * replayed on later calls; a new set of frame pointers only updates the
- * graph's kernel node.  Results are bit-identical to glint_eval per frame.
+ * launch over the concatenated tiles of all frames - persistent CTAs taking
+ * 1-tile work items from a counter, or one CTA per tile, whichever the tuner
+ * finds faster - so frames of uneven size and cost balance across the GPU.
+ * The launch is recorded in a CUDA graph (counter reset + kernel) owned by
+ * the context and replayed on later calls; a new set of frame pointers only
+ * updates the graph's kernel node (a switch between n_rings = 0 and > 0
+ * records it again).  Results are bit-identical to glint_eval per frame.
  *
  * Context: created on the current device; owns a 4-byte device counter, an
  * internal stream and the graph.  Not thread-safe; batches of one context
