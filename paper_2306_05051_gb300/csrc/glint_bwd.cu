@@ -154,7 +154,7 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
     float gm[3] = {0.0f, 0.0f, 0.0f};         // alpha_x, alpha_y, ln density
     for (int l = 0; l < F.nL; ++l) {
         LightState L;
-        setup_light<true>(P, F, S, px, l, L);
+        setup_light<false>(P, F, S, px, l, L);          // no angular texel record needed
         if (!L.on) continue;
         LightGrad LG;
         light_grad(P, F, S, px, l, L, LG);
