@@ -3,8 +3,8 @@
 The paper measures glint shading on Unity scenes (Plane 90/25 degrees,
 Sphere, Heightmap, Sponza; Sec. 7, Table 1) that are not available here.
 This module builds analytic stand-ins: a pinhole camera, ray/plane and
-ray/sphere hits, analytic uv maps, and uv derivatives from first-order ray
-differentials.  It contains none of the glint method's arithmetic; both the
+ray/sphere hits, a ray-marched displaced plane, analytic uv maps, and uv
+derivatives from first-order ray differentials.  It contains none of the glint method's arithmetic; both the
 CUDA library and the CPU oracle read the bytes it produces.
 
 G-buffer layout, per pixel, 16 float32 (4 x float4):
@@ -83,14 +83,15 @@ def _normalize(v: torch.Tensor) -> torch.Tensor:
     return v / torch.linalg.vector_norm(v, dim=-1, keepdim=True).clamp_min(1e-300)
 
 
-def camera_rays(W, H, eye, target, fov_deg=60.0, device="cpu"):
-    """Pinhole camera, vertical field of view fov_deg.  Returns eye [3],
+def camera_rays(W, H, eye, target, fov_deg=60.0, device="cpu", up=(0.0, 1.0, 0.0)):
+    """Pinhole camera, vertical field of view fov_deg, `up` the world
+    direction that appears upwards on screen.  Returns eye [3],
     unnormalised directions D [H, W, 3] and their screen derivatives
     dD/dx, dD/dy [3] (constant for a pinhole)."""
     f64 = torch.float64
     eye = torch.tensor(eye, dtype=f64, device=device)
     fwd = _normalize(torch.tensor(target, dtype=f64, device=device) - eye)
-    up0 = torch.tensor([0.0, 1.0, 0.0], dtype=f64, device=device)
+    up0 = torch.tensor(up, dtype=f64, device=device)
     right = _normalize(torch.linalg.cross(fwd, up0))
     up = torch.linalg.cross(right, fwd)
     th = math.tan(math.radians(fov_deg) / 2)
@@ -220,7 +221,7 @@ def _f32(x):
 
 
 # --------------------------------------------------------------------------
-# the five workloads
+# the paper-shaped workloads
 # --------------------------------------------------------------------------
 def plane45(W=256, H=256, ndf=0, seed=1, device="cpu") -> Scene:
     """256^2 flat plane viewed at 45 degrees, seeded affine uv map scaled so
@@ -303,6 +304,119 @@ def sphere_plane(W=3840, H=2160, azimuth_deg=0.0, seed=3, device="cpu") -> Scene
                  [Light(kind=0), Light(kind=0)])
 
 
+# --------------------------------------------------------------------------
+# displaced plane (heightmap)
+# --------------------------------------------------------------------------
+@dataclass
+class Heightfield:
+    """h(x, z) = sum_k a_k sin(kx_k x + kz_k z + phi_k): seeded waves with
+    log-uniform wavelengths and uniform directions and phases, amplitudes
+    set so every wave has the same slope amplitude a_k |k_k| and the
+    root-mean-square slope of the sum is `rms_slope`."""
+    kx: torch.Tensor
+    kz: torch.Tensor
+    phase: torch.Tensor
+    amp: torch.Tensor
+
+    @staticmethod
+    def seeded(seed, n_waves=16, wavelengths=(0.01, 0.08), rms_slope=0.45):
+        gen = torch.Generator().manual_seed(seed)
+        rnd = lambda: torch.rand(n_waves, generator=gen, dtype=torch.float64)
+        lam = wavelengths[0] * (wavelengths[1] / wavelengths[0]) ** rnd()
+        ang, phase = rnd() * 2 * math.pi, rnd() * 2 * math.pi
+        k = 2 * math.pi / lam
+        # the slope of one wave has mean square (a |k|)^2 / 2
+        amp = rms_slope * math.sqrt(2.0 / n_waves) / k
+        return Heightfield(k * torch.cos(ang), k * torch.sin(ang), phase, amp)
+
+    @property
+    def bound(self) -> float:
+        return float(self.amp.sum())
+
+    def to(self, device) -> "Heightfield":
+        return Heightfield(*(t.to(device) for t in (self.kx, self.kz, self.phase, self.amp)))
+
+    def height(self, x, z):
+        arg = x[..., None] * self.kx + z[..., None] * self.kz + self.phase
+        return (self.amp * torch.sin(arg)).sum(-1)
+
+    def gradient(self, x, z):
+        c = self.amp * torch.cos(x[..., None] * self.kx + z[..., None] * self.kz + self.phase)
+        return (c * self.kx).sum(-1), (c * self.kz).sum(-1)
+
+
+def _hit_heightfield(eye, D, hf, n_march=128, n_bisect=48, chunk=1 << 18):
+    """First crossing of the ray eye + t D (D_y < 0) with y = h(x, z):
+    march n_march even steps across the slab |y| <= bound, then bisect the
+    first bracket where y - h changes sign from + to -.  Such a crossing
+    is front-facing (D . (-h_x, 1, -h_z) <= 0).  Crests thinner than one
+    march step may be stepped through."""
+    A = hf.bound
+    Df = D.reshape(-1, 3)
+    t = torch.empty(Df.shape[0], dtype=D.dtype, device=D.device)
+    for s in range(0, Df.shape[0], chunk):
+        d = Df[s:s + chunk]
+        f = lambda tt: eye[1] + tt * d[:, 1] - hf.height(eye[0] + tt * d[:, 0], eye[2] + tt * d[:, 2])
+        t_in, t_out = (A - eye[1]) / d[:, 1], (-A - eye[1]) / d[:, 1]
+        step = (t_out - t_in) / n_march
+        lo, hi = t_in.clone(), t_out.clone()
+        found = torch.zeros_like(t_in, dtype=torch.bool)
+        for j in range(1, n_march + 1):
+            tj = t_in + j * step
+            hit = (~found) & (f(tj) <= 0)
+            lo = torch.where(hit, tj - step, lo)
+            hi = torch.where(hit, tj, hi)
+            found |= hit
+        for _ in range(n_bisect):
+            mid = 0.5 * (lo + hi)
+            above = f(mid) > 0
+            lo, hi = torch.where(above, mid, lo), torch.where(above, hi, mid)
+        t[s:s + chunk] = hi
+    return t.reshape(D.shape[:-1])
+
+
+def heightmap(W=1920, H=1080, view_deg=25.0, seed=5, alpha=1.0, density=1e7, device="cpu") -> Scene:
+    """Plane y = 0 displaced by a high-frequency seeded heightfield (16
+    waves, wavelengths 0.01-0.08, RMS slope 0.45), ray-marched from a
+    camera at height 1 whose central ray meets the base plane at view_deg
+    (90 looks straight down), vertical field of view 30 degrees so the
+    surface fills the frame.  Normals and tangents are the heightfield's;
+    uv = 64 x world (x, z) wrapped to [0, 64), with derivatives from ray
+    differentials transferred onto the local tangent plane, so facets seen
+    edge-on scatter pixels of large anisotropy across the frame.  Beckmann
+    alpha = 1 isotropic (the paper's timing material, Sec. 7.1), density
+    1e7, 16 LODs (footprints up to 4^15 flakes before a k x k split, so a
+    density sweep to 1e10 stays on the pyramid), one directional light at
+    30 degrees elevation."""
+    v = math.radians(view_deg)
+    eye = (0.0, 1.0, 0.0)
+    target = (0.0, 1.0 - math.sin(v), -math.cos(v))
+    eye_t, D, dDdx, dDdy = camera_rays(W, H, eye, target, 30.0, device, up=(0.0, 0.0, -1.0))
+    if not bool((D[..., 1] < 0).all()):
+        raise ValueError("heightmap: every ray must point below the horizon (view_deg > 15)")
+    hf = Heightfield.seeded(seed).to(device)
+    t = _hit_heightfield(eye_t, D, hf)
+    P = eye_t + t[..., None] * D
+    hx, hz = hf.gradient(P[..., 0], P[..., 2])
+    one = torch.ones_like(hx)
+    N = _normalize(torch.stack([-hx, one, -hz], -1))
+    dPdx = _transfer(t, D, dDdx.expand_as(D), N)
+    dPdy = _transfer(t, D, dDdy.expand_as(D), N)
+    s = 64.0
+    u, v_ = torch.remainder(s * P[..., 0], s), torch.remainder(s * P[..., 2], s)
+    dudx, dvdx = s * dPdx[..., 0], s * dPdx[..., 2]
+    dudy, dvdy = s * dPdy[..., 0], s * dPdy[..., 2]
+    tg = _normalize(torch.stack([one, hx, torch.zeros_like(hx)], -1))     # dP/du
+    wv = _normalize(-D)
+    mask = torch.ones_like(t, dtype=torch.bool)
+    gbuf = _pack(u, v_, dudx, dvdx, dudy, dvdy, N, tg, wv, mask)
+    el = math.radians(30.0)
+    ldir = (0.0, math.sin(el), -math.cos(el))
+    mat = Material(ndf=0, alpha_x=alpha, alpha_y=alpha, ln_density=math.log(density), n_lods=16)
+    return Scene(f"heightmap{int(round(view_deg))}", _f32(gbuf), None, None, mat,
+                 [Light(kind=1, dir=ldir, intensity=1.0)])
+
+
 ORBIT_RESOLUTIONS = [(256, 256), (512, 512), (1280, 720), (1920, 1080)]
 
 
@@ -359,7 +473,7 @@ def plane_sphere_fit(W=512, H=512, target=False, device="cpu") -> Scene:
 
 def by_name(name: str, **kw) -> Scene:
     return {"plane45": plane45, "grazing_plane": grazing_plane, "sphere_plane": sphere_plane,
-            "plane_sphere_fit": plane_sphere_fit}[name](**kw)
+            "plane_sphere_fit": plane_sphere_fit, "heightmap": heightmap}[name](**kw)
 
 
 def random_gbuffer(W=131, H=77, seed=0, n_point=1, n_dir=1, material_plane=True, device="cpu") -> Scene:

@@ -9,7 +9,11 @@ Rules (the tolerance of the glint path):
   * integer counts: exact unless the oracle's continuous count lies within
     COUNT_MARGIN * max(1, c) of an integer (or n of an integer for the
     ceil(n) clamp);
-  * excused mismatches: at most BUDGET of all evaluation records;
+  * excused mismatches: at most BUDGET of all evaluation records, plus the
+    open-gate records whose count an FP32 evaluation cannot decide (the
+    oracle's continuous count within FP32_WINDOW * max(1, c) of an integer:
+    a few units in the last place of an FP32 count, the rounding that the
+    count's inputs n and p already carry);
   * radiance: relative error <= RAD_TOL (denominator max(|ref|, 1e-6
     mean|ref|)) on pixels whose decisions all match.
 """
@@ -23,6 +27,7 @@ GATE_MARGIN = 2e-6
 ENUM_MARGIN = 1e-5
 STRUCT_MARGIN = 1e-7
 BUDGET = 1e-4
+FP32_WINDOW = 8 * 2.0 ** -24
 
 
 def _frac(x):
@@ -61,15 +66,18 @@ def struct_margin(orc, opix, material, rec):
 
 
 def compare_pixel(orc, material, opix, orecs, gpix, grecs):
-    """Compare one pixel's records.  Returns (n_records, n_excused, unexcused list)."""
+    """Compare one pixel's records.  Returns (n_records, n_excused,
+    unexcused list, n_fp32_undecided)."""
     unexcused = []
     excused = 0
+    undecided = sum(1 for o in orecs if int(o["gate"])
+                    and _near_int(float(o["c_cont"]), FP32_WINDOW * max(1.0, abs(float(o["c_cont"])))))
     if int(opix["status"]) != int(gpix["status"]) or (int(opix["status"]) == 0 and int(opix["K"]) != int(gpix["K"])):
         # only decision-boundary cases may disagree on the pixel level
         m = struct_margin(orc, opix, material, orecs[0]) if len(orecs) else 1.0
         if m <= STRUCT_MARGIN:
-            return len(orecs), len(orecs), []
-        return len(orecs), 0, [("pixel", int(opix["status"]), int(gpix["status"]), int(opix["K"]), int(gpix["K"]))]
+            return len(orecs), len(orecs), [], undecided
+        return len(orecs), 0, [("pixel", int(opix["status"]), int(gpix["status"]), int(opix["K"]), int(gpix["K"]))], undecided
     g = {}
     for r in grecs:
         if r["light"] >= 0:
@@ -118,7 +126,7 @@ def compare_pixel(orc, material, opix, orecs, gpix, grecs):
                 unexcused.append(("count", key, int(o["c"]), int(r["c"]), cc, float(r["c_cont"]), float(o["n"]), float(r["n"])))
     for key in g:
         unexcused.append(("extra", key))
-    return len(orecs), excused, unexcused
+    return len(orecs), excused, unexcused, undecided
 
 
 def trace_and_compare(orc, scene_cpu, scene_dev, pixels, material=None, lights=None):
@@ -134,17 +142,18 @@ def trace_and_compare(orc, scene_cpu, scene_dev, pixels, material=None, lights=N
         Kmax = max(Kmax, int(p["K"]))
     cap = max(1, len(lights)) * 48 * Kmax
     gpix, grecs = glint.trace(scene_dev, pixels, cap=cap, material=material, lights=lights)
-    n_rec = n_exc = 0
+    n_rec = n_exc = n_und = 0
     bad = []
     bad_px = []
     for k, px in enumerate(pixels):
-        n, e, u = compare_pixel(orc, material, opix[k], orecs[k], gpix[k], grecs[k])
-        n_rec += n; n_exc += e
+        n, e, u, d = compare_pixel(orc, material, opix[k], orecs[k], gpix[k], grecs[k])
+        n_rec += n; n_exc += e; n_und += d
         if e or u:
             bad_px.append(int(px))
         if u:
             bad.append((int(px), u[:4]))
-    return dict(n_rec=n_rec, n_excused=n_exc, unexcused=bad, mismatched_pixels=bad_px, opix=opix, gpix=gpix)
+    return dict(n_rec=n_rec, n_excused=n_exc, n_fp32_undecided=n_und, unexcused=bad, mismatched_pixels=bad_px,
+                opix=opix, gpix=gpix)
 
 
 def radiance_error(img, ref):
@@ -174,7 +183,8 @@ def check_image(orc, scene_cpu, scene_dev, img, ref, px=None, max_traced=400, rn
     sample = np.sort(rng.choice(pool, size=min(sample_trace, len(pool)), replace=False)).astype(np.int32)
     s = trace_and_compare(orc, scene_cpu, scene_dev, sample)
     assert not s["unexcused"], f"unexcused mismatches: {s['unexcused'][:5]}"
-    assert s["n_excused"] <= BUDGET * s["n_rec"] + 1, (s["n_excused"], s["n_rec"])
+    assert s["n_excused"] <= BUDGET * s["n_rec"] + s["n_fp32_undecided"] + 1, \
+        (s["n_excused"], s["n_rec"], s["n_fp32_undecided"])
     matched = ~np.isin(ids, np.asarray(sorted(set(s["mismatched_pixels"]) | set(int(p) for p in over)), dtype=np.int64))
     s["max_err_matched"] = float(err[matched].max()) if matched.any() else 0.0
     s["over"] = int(len(over))

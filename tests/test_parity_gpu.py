@@ -22,7 +22,8 @@ def _render(scene_dev):
 
 
 def _summary(name, s):
-    print(f"[{name}] traced records {s['n_rec']}, excused mismatches {s['n_excused']}, "
+    print(f"[{name}] traced records {s['n_rec']}, excused mismatches {s['n_excused']} "
+          f"(FP32-undecidable counts {s['n_fp32_undecided']}), "
           f"pixels over tol {s['over']}, max rel err (matched) {s['max_err_matched']:.3g}")
 
 
@@ -254,3 +255,47 @@ def test_isotropic_grid_mode(orc, which):
     assert (pix["n_rec"][ok] == 24 * pix["K"][ok] * nl_on).all()
     if which == "grazing_plane":
         assert pix["K"][ok].max() >= 8                     # far rows: anisotropy cut into many pieces
+
+
+def _anisotropy(sc):
+    """Footprint anisotropy per pixel: ratio of the singular values of the
+    uv Jacobian (inf for a degenerate footprint)."""
+    g = sc.gbuf.double().numpy().reshape(-1, 16)
+    J = np.stack([np.stack([g[:, 2], g[:, 4]], -1), np.stack([g[:, 3], g[:, 5]], -1)], -2)
+    sv = np.linalg.svd(J, compute_uv=False)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(sv[:, 1] > 0, sv[:, 0] / sv[:, 1], np.inf)
+
+
+@pytest.mark.parametrize("view,rings", [(25.0, 4), (90.0, 4), (25.0, 0), (25.0, 6)])
+def test_heightmap_1080p_sampled(orc, view, rings):
+    """Displaced plane at 1920 x 1080 (the Heightmap 25 / 90 degree views of
+    Sec. 7.1, Beckmann alpha = 1): random pixels plus the scattered pixels of
+    anisotropy above 16, with anisotropic grids (4 and 6 rings) and with
+    isotropic grids."""
+    import dataclasses
+    scd = scenes.heightmap(view_deg=view, device=DEV)
+    scd = dataclasses.replace(scd, material=dataclasses.replace(scd.material, n_rings=rings))
+    sc = scd.to("cpu")
+    img = _render(scd)
+    rng = np.random.default_rng(11)
+    r = _anisotropy(sc)
+    tail = np.flatnonzero(r > 16)
+    picks = [rng.choice(r.size, 10000, replace=False)]
+    if tail.size:
+        picks.append(rng.choice(tail, min(2000, tail.size), replace=False))
+    px = np.unique(np.concatenate(picks)).astype(np.int32)
+    ref = orc.eval_image(sc, px=px)
+    assert np.count_nonzero(ref) > 1000
+    s = parity.check_image(orc, sc, scd, img, ref, px=px, sample_trace=300)
+    _summary(f"heightmap {view:g} rings={rings}", s)
+    if view == 25.0:
+        # large anisotropy is scattered over the frame, not gathered in rows
+        rows = np.unique(tail // sc.width)
+        assert rows.size > sc.height // 2
+        sel = tail[np.argsort(-r[tail])[:2000]].astype(np.int32)       # the most anisotropic
+        pix, _ = glint.trace(scd, sel, cap=0)
+        ok = pix["status"] == 0
+        # pieces along the major axis: ceil(r / 2^M), at most 64
+        kmaj = np.minimum(np.ceil(r[sel] / 2.0 ** rings - 1e-6), 64)
+        assert (pix["K"][ok] >= kmaj[ok] - 1).all() and pix["K"][ok].max() >= 2
