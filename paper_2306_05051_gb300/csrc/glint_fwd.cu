@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KPara
         __syncthreads();
         const int px = base + tile_pixel();
         const float o = shade_warp<kIso>(P, T, F, q, px, px < F.npx, ss0, suw);
-        if (px < F.npx) F.out[px] = o;
+        if (px < F.npx) __stcs(F.out + px, o);
     }
 }
 
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KPa
         const FrameDesc& F = B.frames[lo];
         const int px = (t - B.tile_base[lo]) * (int)blockDim.x + tile_pixel();
         const float o = shade_warp<kIso>(P, T, F, q, px, px < F.npx, ss0, suw);
-        if (px < F.npx) F.out[px] = o;
+        if (px < F.npx) __stcs(F.out + px, o);
     }
 }
 

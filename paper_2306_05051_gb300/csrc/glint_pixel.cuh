@@ -182,9 +182,11 @@ struct PixelSetup {
     float ax, ay, cos_v, lam_v;
 };
 
+// The input planes are read once per launch: streaming (evict-first) loads
+// leave the L2 to the per-thread stack of the setup state.
 __device__ __forceinline__ bool load_gbuf(const FrameDesc& F, int px, float4& g0, float4& g1, float4& g2, float4& g3) {
     const float4* g = F.gbuf + (size_t)px * 4;
-    g0 = __ldg(g); g1 = __ldg(g + 1); g2 = __ldg(g + 2); g3 = __ldg(g + 3);
+    g0 = __ldcs(g); g1 = __ldcs(g + 1); g2 = __ldcs(g + 2); g3 = __ldcs(g + 3);
     const float gv[15] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z};
     bool finite = true;
 #pragma unroll
@@ -237,7 +239,7 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
     S.srho = ldf(P.sqrt_rho);
     S.ax = P.ax; S.ay = P.ay;
     if (F.mat_px) {
-        const float2 mp = __ldg(F.mat_px + px);
+        const float2 mp = __ldcs(F.mat_px + px);
         S.ax = S.ay = mp.x;
         rho = mkdf(mp.y);
         S.srho = dfsqrt(rho);
@@ -408,7 +410,7 @@ static __device__ __forceinline__ void setup_light(const KParams& P, const Frame
     const KLight kl = P.lights[l];
     float lr[3], E;
     if (kl.kind == 0) {
-        const float4 lp = __ldg(F.light_px + (size_t)l * F.lstride + px);
+        const float4 lp = __ldcs(F.light_px + (size_t)l * F.lstride + px);
         lr[0] = lp.x; lr[1] = lp.y; lr[2] = lp.z; E = lp.w;
     } else {
         lr[0] = kl.dx; lr[1] = kl.dy; lr[2] = kl.dz; E = kl.E;
