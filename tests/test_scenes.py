@@ -56,3 +56,35 @@ def test_heightmap_first_hit_lies_on_the_surface():
         Q = eye + tt[..., None] * D
         earlier |= (Q[..., 1] - hf.height(Q[..., 0], Q[..., 2])) < -1e-9
     assert float(earlier.double().mean()) < 0.01
+
+
+def test_heightmap_uv_derivatives_match_finite_differences():
+    """The stored du/dx ... dv/dy are the first-order ray differentials of
+    the ray-marched hit: compare with central differences of hits of rays
+    moved by +-1e-5 pixel (same crossing, so the difference is smooth; at
+    grazing pixels a 1e-3 pixel step is already off by the curvature)."""
+    W, H, view = 96, 54, 25.0
+    v = math.radians(view)
+    eye, D, dDdx, dDdy = scenes.camera_rays(W, H, (0.0, 1.0, 0.0), (0.0, 1.0 - math.sin(v), -math.cos(v)), 30.0,
+                                            up=(0.0, 0.0, -1.0))
+    sc = scenes.heightmap(W, H, view_deg=view)
+    hf = scenes.Heightfield.seeded(5)
+    g = sc.gbuf.double()
+    rng = np.random.default_rng(3)
+    ys, xs = rng.integers(0, H, 60), rng.integers(0, W, 60)
+    d = 1e-5
+    checked = 0
+    for y, x in zip(ys, xs):
+        n, wv = g[y, x, 6:9], g[y, x, 12:15]
+        if float((n * wv).sum()) < 0.2:        # near-silhouette: a nearby ray may hit another facet
+            continue
+        rays = torch.stack([D[y, x] + d * dDdx, D[y, x] - d * dDdx, D[y, x] + d * dDdy, D[y, x] - d * dDdy])
+        t = scenes._hit_heightfield(eye, rays[:, None, :], hf)[:, 0]
+        P = eye + t[:, None] * rays
+        uv = 64.0 * P[:, [0, 2]]
+        du_dx, du_dy = (uv[0] - uv[1]) / (2 * d), (uv[2] - uv[3]) / (2 * d)
+        J = torch.tensor([[g[y, x, 2], g[y, x, 4]], [g[y, x, 3], g[y, x, 5]]], dtype=torch.float64)
+        fd = torch.stack([du_dx, du_dy], -1)                   # rows u, v; columns x, y
+        assert torch.allclose(fd, J, rtol=1e-3, atol=1e-4 * float(J.abs().max())), (y, x, fd, J)
+        checked += 1
+    assert checked > 30
