@@ -375,7 +375,8 @@ def _hit_heightfield(eye, D, hf, n_march=128, n_bisect=48, chunk=1 << 18):
     return t.reshape(D.shape[:-1])
 
 
-def heightmap(W=1920, H=1080, view_deg=25.0, seed=5, alpha=1.0, density=1e7, device="cpu") -> Scene:
+def heightmap(W=1920, H=1080, view_deg=25.0, seed=5, alpha=1.0, density=1e7, rms_slope=0.45,
+              device="cpu") -> Scene:
     """Plane y = 0 displaced by a high-frequency seeded heightfield (16
     waves, wavelengths 0.01-0.08, RMS slope 0.45), ray-marched from a
     camera at height 1 whose central ray meets the base plane at view_deg
@@ -387,14 +388,15 @@ def heightmap(W=1920, H=1080, view_deg=25.0, seed=5, alpha=1.0, density=1e7, dev
     alpha = 1 isotropic (the paper's timing material, Sec. 7.1), density
     1e7, 16 LODs (footprints up to 4^15 flakes before a k x k split, so a
     density sweep to 1e10 stays on the pyramid), one directional light at
-    30 degrees elevation."""
+    30 degrees elevation.  rms_slope = 0 gives the flat plane of the same
+    views (the Plane 90 / 25 degree scenes of Table 1)."""
     v = math.radians(view_deg)
     eye = (0.0, 1.0, 0.0)
     target = (0.0, 1.0 - math.sin(v), -math.cos(v))
     eye_t, D, dDdx, dDdy = camera_rays(W, H, eye, target, 30.0, device, up=(0.0, 0.0, -1.0))
     if not bool((D[..., 1] < 0).all()):
         raise ValueError("heightmap: every ray must point below the horizon (view_deg > 15)")
-    hf = Heightfield.seeded(seed).to(device)
+    hf = Heightfield.seeded(seed, rms_slope=rms_slope).to(device)
     t = _hit_heightfield(eye_t, D, hf)
     P = eye_t + t[..., None] * D
     hx, hz = hf.gradient(P[..., 0], P[..., 2])
@@ -413,7 +415,8 @@ def heightmap(W=1920, H=1080, view_deg=25.0, seed=5, alpha=1.0, density=1e7, dev
     el = math.radians(30.0)
     ldir = (0.0, math.sin(el), -math.cos(el))
     mat = Material(ndf=0, alpha_x=alpha, alpha_y=alpha, ln_density=math.log(density), n_lods=16)
-    return Scene(f"heightmap{int(round(view_deg))}", _f32(gbuf), None, None, mat,
+    name = "heightmap" if rms_slope > 0 else "plane"
+    return Scene(f"{name}{int(round(view_deg))}", _f32(gbuf), None, None, mat,
                  [Light(kind=1, dir=ldir, intensity=1.0)])
 
 

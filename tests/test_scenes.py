@@ -88,3 +88,18 @@ def test_heightmap_uv_derivatives_match_finite_differences():
         assert torch.allclose(fd, J, rtol=1e-3, atol=1e-4 * float(J.abs().max())), (y, x, fd, J)
         checked += 1
     assert checked > 30
+
+
+def test_flat_plane_views():
+    """rms_slope = 0: the flat plane of the same views (Table 1's Plane
+    scenes); seen from above every footprint is isotropic, at 25 degrees
+    the anisotropy is 1/sin of the grazing angle, about 1.5 to 6.5."""
+    for view, lo, hi in ((90.0, 1.0 - 1e-6, 1.0 + 1e-6), (25.0, 1.4, 7.0)):
+        sc = scenes.heightmap(160, 90, view_deg=view, rms_slope=0.0)
+        assert sc.name == f"plane{int(view)}"
+        g = sc.gbuf.double().reshape(-1, 16)
+        assert torch.equal(g[:, 6:9], torch.tensor([0.0, 1.0, 0.0], dtype=torch.float64).expand(len(g), 3).abs())
+        J = torch.stack([torch.stack([g[:, 2], g[:, 4]], -1), torch.stack([g[:, 3], g[:, 5]], -1)], -2)
+        sv = torch.linalg.svdvals(J)
+        r = sv[:, 0] / sv[:, 1]
+        assert float(r.min()) >= lo and float(r.max()) <= hi
