@@ -446,6 +446,13 @@ def run_heightmap(args, dev):
         for mode, _ in modes:
             res[surface][f"{mode}_25_over_90_time_max"] = (res[surface]["view_25"][mode]["ms_min_max"][1]
                                                            / res[surface]["view_90"][mode]["ms_min_max"][1])
+    # context, not a target: the paper's own method in Table 1 (RTX 2080, Unity, 1920x1080, whole-frame
+    # ms over its density sweep) and that minus the frame without glints
+    res["paper_table1_rtx2080_ms"] = {
+        "plane_view_90": {"frame": [1.15, 1.25], "glints_only": [0.66, 0.76]},
+        "plane_view_25": {"frame": [1.15, 1.26], "glints_only": [0.66, 0.77]},
+        "heightmap_view_90": {"frame": [1.52, 1.63], "glints_only": [1.01, 1.12]},
+        "heightmap_view_25": {"frame": [1.44, 1.54], "glints_only": [0.93, 1.03]}}
     return res
 
 
