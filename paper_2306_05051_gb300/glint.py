@@ -44,6 +44,8 @@ def render(gbuf: torch.Tensor, light_px: Optional[torch.Tensor] = None, mat_px: 
     """Glint radiance [H, W] of one G-buffer frame (glint_eval; with
     launch = (threads_per_cta, ctas_per_sm), glint_eval_launch)."""
     _check_plane(gbuf, "gbuf", (16,))
+    if gbuf.dim() != 3:
+        raise ValueError(f"gbuf has shape {tuple(gbuf.shape)}, expected [H, W, 16]")
     dev = gbuf.device
     H, W = int(gbuf.shape[0]), int(gbuf.shape[1])
     _check_plane(light_px, "light_px", (H, W, 4), dev)
