@@ -33,8 +33,13 @@ if ROOT not in sys.path:
 METRIC = "glint-shaded Gpixel/s at 4K (fwd, batched vs plain) + fwd+bwd ms; % of roofline"
 WORKLOAD = "sphere_plane 3840x2160, 2 point lights, per-pixel alpha U[0.05,0.5] and log10 density U[3,9], 12 LODs"
 
-# Algorithmic lane-operations of the method as specified, counted as the
-# minimal FP32 / INT32 operations of each step (see the design notes):
+# Algorithmic work per unit, from the hot-path scope table: about 3-3.5 k
+# issued lane instructions per shaded pixel and light (48 evaluations of ~40
+# hash + ~20 quantile + ~8 gate/floor/accumulate operations, plus ~400 of
+# setup); the midpoint is the roofline's unit.
+OPS_PER_PIXEL_LIGHT_SCOPE = 3250
+# A lower bound kept beside it: the minimal FP32 / INT32 operations of each
+# step of the method as specified (see the design notes):
 OPS_PER_PIXEL = 120        # frame, footprint SVD / atan2 / log2, split
 OPS_PER_SUB = 350          # LOD, cell, tetrahedron, 4 grid transforms + simplex, 12 spatial hashes
 OPS_PER_SUB_ISO = 200      # the same with 2 grid vertices (isotropic-grid mode)
@@ -64,21 +69,40 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes (read + write) per fwd_kernel launch from the committed ncu
-    summary, or None if it was captured on other kernel sources."""
+PROFILE_KEYS = ("source_hash", "dram_bytes_per_launch", "issue_active", "pipe_alu", "pipe_fma", "pipe_xu",
+                "pipe_lsu", "warps_active", "registers")
+
+
+def profiled_counters():
+    """Counters of the committed ncu summary of the image kernel (DRAM bytes
+    per launch, issue-active fraction, pipe utilisations), or None if it was
+    captured on other kernel sources."""
+    kv = {}
     try:
         with open(PROFILE) as fh:
-            kv = dict(l.strip().strip("-* `").split(":", 1) for l in fh if l.strip().strip("-* `").startswith(
-                ("source_hash:", "dram_bytes_per_launch:")))
-    except (OSError, ValueError):
+            for l in fh:
+                t = l.strip().strip("-* ")
+                if ":" in t and t.split(":", 1)[0].strip("` ") in PROFILE_KEYS:
+                    k, v = t.split(":", 1)
+                    kv[k.strip("` ")] = v.strip(" `")
+    except OSError:
         return None
-    if kv.get("source_hash", "").strip(" `") != kernel_source_hash():
+    if kv.get("source_hash") != kernel_source_hash():
         return None
-    try:
-        return int(kv["dram_bytes_per_launch"].strip(" `"))
-    except (KeyError, ValueError):
-        return None
+    out = {}
+    for k, v in kv.items():
+        if k == "source_hash":
+            continue
+        try:
+            out[k] = int(v) if k in ("dram_bytes_per_launch", "registers") else float(v)
+        except ValueError:
+            pass
+    return out
+
+
+def profiled_traffic():
+    c = profiled_counters()
+    return None if c is None else c.get("dram_bytes_per_launch")
 
 
 def _peaks():
@@ -208,16 +232,29 @@ def run_ours(args, rank, world, dev):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
+    # the timed loop covers at least a second (and at least --steps steps),
+    # so that the clock sampler sees the GPU under load
+    ev0.record(stream)
+    for _ in range(args.warmup):
+        glint.render_scene(scd, out=out, stream=stream)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_est = ev0.elapsed_time(ev1) / args.warmup
+    n_steps = max(args.steps, int(math.ceil(1000.0 / max(ms_est, 1e-3))))
+    n_steps = int(max_over_ranks(n_steps, dev))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
     with ClockSampler(torch.cuda.current_device()) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(n_steps):
             glint.render_scene(scd, out=out, stream=stream)
         ev1.record(stream)
         ev1.synchronize()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ev0.elapsed_time(ev1) / n_steps
     ms_all = max_over_ranks(ms, dev)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
@@ -241,7 +278,7 @@ def run_ours(args, rank, world, dev):
 
     cen = census(glint, scd)
     return dict(ms=ms_all, e2e_ms=e2e_ms, h2d=h2d, d2h=d2h, npx=npx, census=cen, clocks=clk.summary(),
-                bytes=frame_bytes(scd))
+                bytes=frame_bytes(scd), steps=n_steps)
 
 
 def peak_lane_ops():
@@ -250,10 +287,16 @@ def peak_lane_ops():
     return SMS * LANES_PER_SM * mhz * 1e6 / 1e12
 
 
-def roofline_of(ops, ms):
+def roofline_of(cen, ms, factor=1.0):
+    """ALU roofline of `factor` x the work of census `cen` in ms: the scope
+    table's 3250 lane-ops per pixel-light, and the minimal-op count beside it."""
+    peak = peak_lane_ops()
+    ops = OPS_PER_PIXEL_LIGHT_SCOPE * cen["pl"] * factor
     a = ops / (ms * 1e-3) / 1e12
-    return {"bound": "alu", "achieved": a, "peak": peak_lane_ops(), "unit": "T lane-op/s",
-            "frac": a / peak_lane_ops(), "algorithmic_ops": ops}
+    a_min = cen["ops"] * factor / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": a, "peak": peak, "unit": "T lane-op/s", "frac": a / peak,
+            "algorithmic_ops": ops, "ops_per_pixel_light": OPS_PER_PIXEL_LIGHT_SCOPE,
+            "frac_minimal_ops": a_min / peak, "minimal_ops": cen["ops"] * factor}
 
 
 def run_batched(args, dev):
@@ -291,12 +334,13 @@ def run_batched(args, dev):
     ms_p = ev0.elapsed_time(ev1) / steps
     launch = ctx.launch
     ctx.close()
-    ops = sum(census(glint, f)["ops"] for f in frames)
+    cens = [census(glint, f) for f in frames]
+    cen = {k: sum(c[k] for c in cens) for k in cens[0]}
     nbytes = sum(frame_bytes(f) for f in frames)
     return {"workload": "orbit of the sphere scene, 64 frames (16 each of 256x256, 512x512, 1280x720, "
                         "1920x1080), 2 point lights, per-pixel material",
             "pixels": npx, "value": npx / (ms_b * 1e-3) / 1e9, "unit": "Gpixel/s", "ms_per_batch": ms_b,
-            "roofline": roofline_of(ops, ms_b), "hbm_gbs": nbytes / (ms_b * 1e-3) / 1e9,
+            "roofline": roofline_of(cen, ms_b), "hbm_gbs": nbytes / (ms_b * 1e-3) / 1e9,
             "plain_value": npx / (ms_p * 1e-3) / 1e9, "plain_ms_per_batch": ms_p,
             "speedup_vs_plain": ms_p / ms_b, "launch": launch, "graph_launches_per_batch": 1,
             "plain_launches_per_batch": len(frames)}
@@ -350,14 +394,14 @@ def run_fwd_bwd(args, dev):
     ev[1].record(stream)
     ev[1].synchronize()
     ms_fused = ev[0].elapsed_time(ev[1]) / steps
-    ops_f = census(glint, sc)["ops"]
+    cen = census(glint, sc)
     return {"workload": "plane_sphere_fit 512x512, directional light, L2 loss vs perturbed-parameter target, "
                         "gradients w.r.t. alpha_x, alpha_y, ln density, light direction",
             "ms_per_step": ms, "backward_ms": ms_b, "gpu_launches_per_step": 3, "torch_launches_per_step": 2,
-            "roofline": roofline_of(ops_f * (2.0 + ADJOINT_FACTOR), ms),
-            "backward_roofline": roofline_of(ops_f * (1.0 + ADJOINT_FACTOR), ms_b),
+            "roofline": roofline_of(cen, ms, 2.0 + ADJOINT_FACTOR),
+            "backward_roofline": roofline_of(cen, ms_b, 1.0 + ADJOINT_FACTOR),
             "fused_ms_per_step": ms_fused, "fused_launches_per_step": 2,
-            "fused_roofline": roofline_of(ops_f * (2.0 + ADJOINT_FACTOR), ms_fused),
+            "fused_roofline": roofline_of(cen, ms_fused, 2.0 + ADJOINT_FACTOR),
             "grad": [float(x) for x in grad.cpu()]}
 
 
@@ -380,7 +424,7 @@ def _grid_modes_entry(glint, sc, m, out, stream, args):
     ms = _time_frames(glint, sc, m, out, stream, args)
     cen = census(glint, sc, material=m)
     return {"ms": ms, "gpixel_s": sc.width * sc.height / (ms * 1e-3) / 1e9, "evals": cen["evals"],
-            "sub_footprints": cen["sub"], "roofline": roofline_of(cen["ops"], ms)}
+            "sub_footprints": cen["sub"], "roofline": roofline_of(cen, ms)}
 
 
 def run_isotropic(args, dev):
@@ -403,6 +447,32 @@ def run_isotropic(args, dev):
     res["isotropic_over_anisotropic_time"] = res["isotropic_grids"]["ms"] / res["anisotropic_grids"]["ms"]
     res["isotropic_over_anisotropic_time_16_lods"] = (res["isotropic_grids_16_lods"]["ms"]
                                                       / res["anisotropic_grids_16_lods"]["ms"])
+    return res
+
+
+def run_ablations(args, dev):
+    """The schemes the paper replaces, as material modes of the same kernel,
+    on the 1080p grazing plane (C2) over a sweep of flake densities: the
+    classical Gaussian / Bernoulli-loop sampler (Sec. 6.3; its cost depends
+    on N and p, Sec. 7.1) against the gated sampler, and the linear mix of
+    LOD outputs (Sec. 3) against the distributed binomial."""
+    import dataclasses
+    from paper_2306_05051_gb300 import glint, scenes
+    sc = scenes.grazing_plane(device=dev)
+    out = torch.empty(sc.height, sc.width, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    res = {"workload": "grazing_plane 1920x1080, directional light, anisotropy to 32:1 (C2), 12 LODs"}
+    for name, kw in (("gated", {}), ("classical", {"sampler": 1}), ("linear_mix", {"lod_blend": 1})):
+        per = {}
+        for rho in (1e3, 1e4, 1e5, 1e6, 1e7):
+            m = dataclasses.replace(sc.material, ln_density=math.log(rho), **kw)
+            per[f"density_{rho:.0e}"] = _time_frames(glint, sc, m, out, stream, args)
+        ms = list(per.values())
+        per["ms_min_max"] = [min(ms), max(ms)]
+        per["max_over_min"] = max(ms) / min(ms)
+        res[name] = per
+    res["classical_over_gated_time"] = {k: res["classical"][k] / res["gated"][k] for k in res["gated"]
+                                        if k.startswith("density_")}
     return res
 
 
@@ -490,7 +560,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fwd-bwd", action="store_true")
     ap.add_argument("--no-isotropic", action="store_true")
-    ap.add_argument("--no-heightmap", action="store_true")
+    ap.add_argument("--no-ablations", action="store_true")
+    ap.add_argument("--heightmap", action="store_true",
+                    help="also time the Plane / Heightmap 90 and 25 degree views at three densities")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -535,38 +607,55 @@ def main():
     value = whole_job_rate(r["npx"], world, r["ms"])
     peaks = _peaks()
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = SMS * LANES_PER_SM * mhz * 1e6 / 1e12          # T lane-ops/s
     cen = r["census"]
-    achieved = cen["ops"] / (r["ms"] * 1e-3) / 1e12
+    roof = roofline_of(cen, r["ms"])
+    ncu = profiled_counters()
+    roof.update({"traffic": None if ncu is None else ncu.get("dram_bytes_per_launch"),
+                 "traffic_source": os.path.relpath(PROFILE, ROOT), "kernel_source_hash": kernel_source_hash(),
+                 "ncu": ncu, "evals_per_launch": cen["evals"], "pixel_lights_per_launch": cen["pl"],
+                 "peak_basis": f"{SMS} SMs x {LANES_PER_SM} FP32/INT32 lanes x {mhz:.0f} MHz",
+                 "hbm_gbs": r["bytes"] / (r["ms"] * 1e-3) / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs")})
     line = {
-        "metric": METRIC, "value": value, "unit": "Gpixel/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": METRIC, "value": value, "unit": "Gpixel/s", "n_gpus": world, "steps": r["steps"],
+        "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "pixels_per_gpu": r["npx"], "l2": "inputs larger than L2 "
                    f"({r['bytes'] / 1e6:.0f} MB read+written per step vs 129 MB L2)",
-                   "parallelism": f"replicas x{world} (one frame per GPU)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "T lane-op/s",
-                     "frac": achieved / peak_ops, "traffic": profiled_traffic(),
-                     "traffic_source": os.path.relpath(PROFILE, ROOT), "kernel_source_hash": kernel_source_hash(),
-                     "algorithmic_ops_per_launch": cen["ops"], "evals_per_launch": cen["evals"],
-                     "peak_basis": f"{SMS} SMs x {LANES_PER_SM} FP32/INT32 lanes x {mhz:.0f} MHz",
-                     "hbm_gbs": r["bytes"] / (r["ms"] * 1e-3) / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs")},
+                   "parallelism": f"replicas x{world} (one frame per GPU)",
+                   "timed_loop": "at least --steps steps and at least 1 s"},
+        "roofline": roof,
         "e2e": {"value": npx_all / (r["e2e_ms"] * 1e-3) / 1e9, "unit": "Gpixel/s",
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"], "ms_per_step": r["e2e_ms"]},
-        "gpu_launches": args.steps,
+        "gpu_launches": r["steps"],
         "clocks": r["clocks"],
         "census": cen,
     }
-    if not args.no_batched:
-        line["batched"] = run_batched(args, dev)
-    if not args.no_fwd_bwd:
-        line["fwd_bwd"] = run_fwd_bwd(args, dev)
-    if not args.no_isotropic:
-        line["isotropic_grids"] = run_isotropic(args, dev)
-    if not args.no_heightmap:
-        line["plane_heightmap"] = run_heightmap(args, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    if args.heightmap:
+        line["plane_heightmap"] = run_heightmap(args, dev)
+    if not args.no_isotropic:
+        line["isotropic_grids"] = run_isotropic(args, dev)
+    if not args.no_ablations:
+        line["ablations"] = run_ablations(args, dev)
+    if not args.no_fwd_bwd:
+        line["fwd_bwd"] = run_fwd_bwd(args, dev)
+    if not args.no_batched:
+        line["batched"] = run_batched(args, dev)
+    # the headline numbers of every leg, last in the line
+    summ = {"fwd_4k_gpixel_s": value, "fwd_4k_ms": r["ms"], "fwd_4k_roofline_frac": roof["frac"],
+            "e2e_4k_gpixel_s": line["e2e"]["value"]}
+    if "batched" in line:
+        b = line["batched"]
+        summ.update({"batched_gpixel_s": b["value"], "batched_ms": b["ms_per_batch"],
+                     "plain_64_launches_ms": b["plain_ms_per_batch"], "batched_speedup": b["speedup_vs_plain"],
+                     "batched_roofline_frac": b["roofline"]["frac"]})
+    if "fwd_bwd" in line:
+        f = line["fwd_bwd"]
+        summ.update({"fwd_bwd_ms": f["ms_per_step"], "backward_ms": f["backward_ms"],
+                     "fit_l2_ms": f["fused_ms_per_step"], "fwd_bwd_roofline_frac": f["roofline"]["frac"],
+                     "fit_l2_roofline_frac": f["fused_roofline"]["frac"]})
+    line["summary"] = summ
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -71,7 +71,33 @@ extern "C" {
  *               powers of two; Sec. 1 says consecutive LODs quadruple).
  *   max_sub     K_max, 1..64: most sub-footprints one pixel is cut into when
  *               its ratio exceeds 2^M or its area exceeds the top level.
- *   seed        32-bit seed of the per-texel hash. */
+ *   seed        32-bit seed of the per-texel hash.
+ *   lod_blend   0: distributed binomial (Sec. 4.2, the paper's method): each
+ *               grid vertex counts w_i N_i trials.  1: linear mix of LOD
+ *               outputs (Sec. 3, "Temporal Coherence", the scheme Sec. 4.2
+ *               replaces): each grid vertex counts over its whole cell and
+ *               its count is weighted by w_i (same mean, smaller variance).
+ *   sampler     0: gated Gaussian approximation (Sec. 6.3, the paper's).
+ *               1: classical approximation (Sec. 6.3, the one it replaces):
+ *               a floored Gaussian of mean N p and variance N p (1 - p)
+ *               sampled at the first hash word where N p > 5 or N > 16, else
+ *               an explicit sum of ceil(N) Bernoulli trials (the last one of
+ *               weight N - floor N) whose uniforms are fmix32(h1 + k
+ *               0x9E3779B9), k = 1..ceil N, of the second word h1.
+ *   rng_table   0: the two uniforms of an evaluation come from mixing its
+ *               spatial and angular hash words (fmix32).  1: they are fetched
+ *               from a precomputed table of 2^16 word pairs (Sec. 6.3, last
+ *               paragraph: a small texture of random numbers), entry
+ *               (s + a) >> 16 of the spatial and angular words; requires
+ *               n_rings > 0 and sampler = 0 (else GLINT_ERR_UNSUPPORTED).  The
+ *               table lives in static device memory of the library, filled
+ *               by the first call that uses it on a device (one kernel and a
+ *               wait for it on the call's stream): make that first call
+ *               before any stream capture.
+ *               lod_blend = 1, sampler = 1 and rng_table = 1 are ablations:
+ *               glint_eval, glint_eval_batch and glint_eval_trace accept
+ *               them; glint_backward and glint_fit_l2 return
+ *               GLINT_ERR_UNSUPPORTED. */
 typedef struct GlintMaterial {
     int32_t  ndf;
     float    alpha_x, alpha_y;
@@ -84,6 +110,9 @@ typedef struct GlintMaterial {
     int32_t  lod_factor;
     int32_t  max_sub;
     uint32_t seed;
+    int32_t  lod_blend;
+    int32_t  sampler;
+    int32_t  rng_table;
 } GlintMaterial;
 
 /* Punctual light (Sec. 8: point lights only; cost linear in lights).
@@ -249,7 +278,9 @@ int glint_fit_l2(const GlintFrame* frame, const GlintMaterial* material, const G
  * GLINT_ERR_WORKSPACE before anything is enqueued.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, once per device, with that device current); make
- *     that first call before any stream capture.
+ *     that first call before any stream capture.  The address is kept for the
+ *     life of the process: after cudaDeviceReset on a device this entry point
+ *     must not be called on that device again.
  *   - Every call uses the same array and clears the counters it needs at the
  *     start (an asynchronous memset on `stream`).  Calls whose work overlaps
  *     on the GPU - on different streams, or from different threads - race on

@@ -40,7 +40,8 @@ class OMaterial(C.Structure):
     _fields_ = [("ndf", C.c_int32), ("alpha_x", C.c_float), ("alpha_y", C.c_float),
                 ("ln_density", C.c_float), ("R", C.c_float), ("F0", C.c_float), ("gamma", C.c_float),
                 ("n_lods", C.c_int32), ("n_rings", C.c_int32), ("lod_factor", C.c_int32),
-                ("max_sub", C.c_int32), ("seed", C.c_uint32)]
+                ("max_sub", C.c_int32), ("seed", C.c_uint32), ("lod_blend", C.c_int32), ("sampler", C.c_int32),
+                ("rng_table", C.c_int32)]
 
 
 class OLight(C.Structure):
@@ -58,7 +59,7 @@ REC_DTYPE = np.dtype([("light", "i4"), ("sub", "i4"), ("vert", "i4"), ("sv", "i4
                       ("n", "f8"), ("p", "f8"), ("P1", "f8"), ("mu", "f8"), ("sigma", "f8"),
                       ("z", "f8"), ("c_cont", "f8"), ("u", "f8"), ("v", "f8"),
                       ("x", "f8"), ("t", "f8"), ("s", "f8"), ("As", "f8"), ("qx", "f8"),
-                      ("qy", "f8"), ("afx", "f8"), ("afy", "f8")], align=True)
+                      ("qy", "f8"), ("afx", "f8"), ("afy", "f8"), ("w", "f8")], align=True)
 
 _P = C.c_void_p
 _D = C.c_double
@@ -81,6 +82,8 @@ def lib():
             L.oracle_eval_hash.argtypes = [C.c_int32, C.c_int32, C.c_uint32, C.c_int32, C.c_int32,
                                            C.c_uint32, _P]
             L.oracle_theta.argtypes = [C.c_uint32]; L.oracle_theta.restype = _D
+            L.oracle_table_words.argtypes = [C.c_uint32, _P]
+            L.oracle_eval_table.argtypes = [C.c_int32, C.c_int32, C.c_uint32, C.c_int32, C.c_int32, C.c_uint32, _P]
             L.oracle_ndf.argtypes = [_I, _D, _D, _D, _D, _D]; L.oracle_ndf.restype = _D
             L.oracle_smith_lambda.argtypes = [_I, _D, _D, _D, _D, _D]; L.oracle_smith_lambda.restype = _D
             L.oracle_footprint.argtypes = [_D, _D, _D, _D, _P]
@@ -91,6 +94,9 @@ def lib():
             L.oracle_grid_coords.argtypes = [_D, _D, _I, _I, _I, _D, _I, _P]
             L.oracle_simplex.argtypes = [_D, _D, _P, _P]
             L.oracle_gated_count.argtypes = [_D, _D, _D, _D, _P]; L.oracle_gated_count.restype = _I
+            L.oracle_exact_count.argtypes = [_I, _D, _D]; L.oracle_exact_count.restype = _I
+            L.oracle_classical_count.argtypes = [_D, _D, C.c_uint32, C.c_uint32, _P]
+            L.oracle_classical_count.restype = _I
             sizes = np.zeros(4, np.int32)
             L.oracle_struct_sizes(sizes.ctypes.data_as(_P))
             assert sizes[0] == C.sizeof(OMaterial) and sizes[1] == C.sizeof(OLight), sizes
@@ -117,7 +123,8 @@ def _ptr(a):
 def _material(m) -> OMaterial:
     return OMaterial(int(m.ndf), float(m.alpha_x), float(m.alpha_y), float(m.ln_density), float(m.R),
                      float(m.F0), float(m.gamma), int(m.n_lods), int(m.n_rings), int(m.lod_factor),
-                     int(m.max_sub), int(m.seed) & 0xFFFFFFFF)
+                     int(m.max_sub), int(m.seed) & 0xFFFFFFFF, int(getattr(m, "lod_blend", 0)),
+                     int(getattr(m, "sampler", 0)), int(getattr(m, "rng_table", 0)))
 
 
 def _lights(lights):
@@ -225,6 +232,19 @@ def eval_hash(i, j, gid, ax, ay, seed):
     return int(h[0]), int(h[1])
 
 
+def table_words(k):
+    h = np.zeros(2, np.uint32)
+    lib().oracle_table_words(int(k) & 0xFFFFFFFF, h.ctypes.data_as(_P))
+    return int(h[0]), int(h[1])
+
+
+def eval_table(i, j, gid, ax, ay, seed):
+    h = np.zeros(2, np.uint32)
+    lib().oracle_eval_table(int(i), int(j), int(gid) & 0xFFFFFFFF, int(ax), int(ay), int(seed) & 0xFFFFFFFF,
+                            h.ctypes.data_as(_P))
+    return int(h[0]), int(h[1])
+
+
 def theta(h):
     return lib().oracle_theta(int(h) & 0xFFFFFFFF)
 
@@ -282,6 +302,19 @@ def simplex(qx, qy):
     i = np.zeros(6, np.int32); w = np.zeros(3)
     lib().oracle_simplex(qx, qy, i.ctypes.data_as(_P), w.ctypes.data_as(_P))
     return [(int(i[2 * k]), int(i[2 * k + 1])) for k in range(3)], w
+
+
+def classical_count(n, p, h0, h1):
+    """(c, z, c_cont) of the classical sampler for words h0, h1."""
+    d = np.zeros(2)
+    c = lib().oracle_classical_count(float(n), float(p), int(h0) & 0xFFFFFFFF, int(h1) & 0xFFFFFFFF,
+                                     d.ctypes.data_as(_P))
+    return int(c), float(d[0]), float(d[1])
+
+
+def exact_count(N, p, theta):
+    """Exact sampler: inverse of the Bin(N, p) CDF at theta (integer N)."""
+    return int(lib().oracle_exact_count(int(N), float(p), float(theta)))
 
 
 def gated_count(n, p, th0, th1):

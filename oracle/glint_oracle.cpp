@@ -99,6 +99,9 @@ struct OMaterial {
     int32_t lod_factor;   /* f (2 or 4) */
     int32_t max_sub;      /* K_max */
     uint32_t seed;
+    int32_t lod_blend;    /* 0 distributed binomial (Sec. 4.2); 1 linear mix of outputs (Sec. 3) */
+    int32_t sampler;      /* 0 gated Gaussian (Sec. 6.3); 1 classical Gaussian / Bernoulli loop (Sec. 6.3) */
+    int32_t rng_table;    /* 0 per-evaluation hash; 1 uniforms fetched from a precomputed table (Sec. 6.3) */
 };
 
 struct OLight {
@@ -123,6 +126,7 @@ struct ORec {              /* one binomial evaluation (for parity traces) */
     int32_t gate, c;
     double n, p, P1, mu, sigma, z, c_cont, u, v;
     double x, t, s, As, qx, qy, afx, afy;
+    double w;              /* tetrahedron weight of the record's grid vertex */
 };
 
 struct Scene {
@@ -208,6 +212,30 @@ void eval_hash(int32_t i, int32_t j, uint32_t gid, int32_t ax, int32_t ay, uint3
     pcg3d(a);
     *h0 = fmix32(s[0] + a[0]);
     *h1 = fmix32(s[1] + a[1]);
+}
+
+/* Random-number table (Sec. 6.3, last paragraph: the two uniforms of an
+ * evaluation fetched from a small precomputed texture of random numbers
+ * instead of being computed).  The table holds 2^16 pairs of words,
+ *   R[k] = (fmix32(2k * 0x9E3779B9 + 0x632BE5AB), fmix32((2k + 1) * 0x9E3779B9 + 0x632BE5AB)),
+ * and the evaluation at spatial key s (first pcg4d word of the lattice
+ * vertex and grid) and angular key a (first pcg3d word of the angular texel)
+ * reads entry (s + a) >> 16: the spatial and angular hashes stay, the
+ * per-evaluation mixing is replaced by the fetch. */
+constexpr int kRngTableBits = 16;
+
+void table_words(uint32_t k, uint32_t* h0, uint32_t* h1) {
+    *h0 = fmix32(2u * k * 0x9E3779B9u + 0x632BE5ABu);
+    *h1 = fmix32((2u * k + 1u) * 0x9E3779B9u + 0x632BE5ABu);
+}
+
+void eval_table(int32_t i, int32_t j, uint32_t gid, int32_t ax, int32_t ay, uint32_t seed,
+                uint32_t* h0, uint32_t* h1) {
+    uint32_t s[4] = {(uint32_t)i, (uint32_t)j, gid, seed};
+    pcg4d(s);
+    uint32_t a[3] = {(uint32_t)ax, (uint32_t)ay, ~seed};
+    pcg3d(a);
+    table_words((s[0] + a[0]) >> (32 - kRngTableBits), h0, h1);
 }
 
 /* Uniform in (0, 1) from the top 24 bits of a hash word. */
@@ -507,6 +535,64 @@ T gated_count(const CountLaw<T>& L, double th0, double th1, bool relaxed,
     return cc;
 }
 
+/* Exact sampler (tests only): the count that the gated law stands in for,
+ * the inverse of the Bin(N, p) cumulative distribution at theta for integer
+ * N >= 0 - the smallest k with P(b <= k) > theta, the PMF summed from k = 0
+ * in log space. */
+int exact_binomial_count(int N, double p, double theta) {
+    if (N <= 0 || p <= 0.0) return 0;
+    if (p >= 1.0) return N;
+    double cdf = 0.0;
+    for (int k = 0; k < N; ++k) {
+        cdf += std::exp(std::lgamma(N + 1.0) - std::lgamma(k + 1.0) - std::lgamma(N - k + 1.0) +
+                        k * std::log(p) + (N - k) * std::log1p(-p));
+        if (theta < cdf) return k;
+    }
+    return N;
+}
+
+/* Classical binomial approximation (Sec. 6.3, "Classical Binomial
+ * Approximation"; the sampler the paper replaces): a Gaussian of the
+ * binomial's own mean N p and variance N p (1 - p) sampled at theta0,
+ * floored, where N p > 5; otherwise an explicit sum of Bernoulli trials.
+ * Readings: a trial succeeds when theta_k < p (the printed H(theta_k - p)
+ * fires with probability 1 - p, the sign slip of the gate); the loop runs
+ * over at most 16 trials (Sec. 7.1: the compared implementation loops up to
+ * N = 16), so N > 16 takes the Gaussian too; a fractional last trial
+ * succeeds with probability p (N - floor N); the Gaussian count is clamped
+ * to [0, ceil N].  The loop's uniforms come from the evaluation's second
+ * word: theta_k of fmix32(h1 + k 0x9E3779B9), k = 1..ceil N.  *c_cont
+ * receives the Gaussian's value, or the loop count plus 1/2 (never at an
+ * integer: a loop count has no continuous value). */
+constexpr int kClassicalLoopMax = 16;
+
+template <class T>
+T classical_count(const T& n, const T& p, uint32_t h0, uint32_t h1, int* c_int, double* z, double* c_cont) {
+    const double nv = val(n), pv = val(p);
+    *z = 0.0;
+    if (nv <= 0.0 || pv <= 0.0) { *c_int = 0; *c_cont = 0.5; return T(0.0); }
+    const double nceil = std::ceil(nv);
+    if (nv * pv > 5.0 || nv > (double)kClassicalLoopMax) {
+        const T mu = n * p;
+        const T sig = sqrt(mu * (1.0 - p));
+        *z = phi_inv(theta_of(h0));
+        const T cc = mu + sig * (*z);
+        *c_cont = val(cc);
+        const double c = std::min(std::max(std::floor(val(cc)), 0.0), nceil);
+        *c_int = c < 2147483647.0 ? (int)c : 2147483647;
+        return T(c);
+    }
+    int c = 0;
+    const int nt = (int)nceil;
+    for (int k = 1; k <= nt; ++k) {
+        const double pk = (k == nt && nceil != nv) ? pv * (nv - std::floor(nv)) : pv;
+        if (theta_of(fmix32(h1 + (uint32_t)k * 0x9E3779B9u)) < pk) ++c;
+    }
+    *c_int = c;
+    *c_cont = c + 0.5;
+    return T((double)c);
+}
+
 /* Isotropic-grid mode (M = 0, Sec. 4 with manual anisotropic filtering): the
  * tetrahedron degenerates to the segment between the two LODs of the single
  * isotropic grid - vertex 0 (lower LOD, weight 1 - s) and vertex 3 (upper LOD,
@@ -619,8 +705,12 @@ T eval_pixel(const Scene& sc, int px, const Seeds& sd, bool relaxed, Trace* tr) 
             V.gid = grid_id(V.level, V.ring, V.kor);
             V.w = tv[i].w;
             /* Trials: w_i times the cell's flake count f^level (Sec. 5.2,
-             * "N_i proportional to its area"); pinned: w_i times A_s. */
-            V.n = S.lod.pinned ? V.w * As : V.w * std::pow((double)M.lod_factor, V.level);
+             * "N_i proportional to its area"); pinned: w_i times A_s.  Linear
+             * mix (Sec. 3, the scheme Sec. 4.2 replaces): every vertex counts
+             * over its whole cell (f^level flakes; pinned: A_s) and its count
+             * is weighted by w_i afterwards. */
+            if (M.lod_blend == 1) V.n = S.lod.pinned ? As : T(std::pow((double)M.lod_factor, V.level));
+            else V.n = S.lod.pinned ? V.w * As : V.w * std::pow((double)M.lod_factor, V.level);
             grid_coords(us, vs, V.level, V.ring, V.kor, rho, M.lod_factor, &V.qx, &V.qy);
             if (std::fabs(val(V.qx)) >= 0x1p30 || std::fabs(val(V.qy)) >= 0x1p30) {
                 delete[] subs;
@@ -685,9 +775,17 @@ T eval_pixel(const Scene& sc, int px, const Seeds& sd, bool relaxed, Trace* tr) 
                 for (int j = 0; j < 3; ++j) {
                     for (int k = 0; k < 4; ++k) {
                         uint32_t h0, h1;
-                        eval_hash(V.sv[j].i, V.sv[j].j, V.gid, axs[k], ays[k], M.seed, &h0, &h1);
+                        if (M.rng_table == 1) eval_table(V.sv[j].i, V.sv[j].j, V.gid, axs[k], ays[k], M.seed, &h0, &h1);
+                        else eval_hash(V.sv[j].i, V.sv[j].j, V.gid, axs[k], ays[k], M.seed, &h0, &h1);
                         int gate, ci; double z, ccont;
-                        const T c = gated_count(law, theta_of(h0), theta_of(h1), relaxed, &gate, &ci, &z, &ccont);
+                        T c;
+                        if (M.sampler == 1) {
+                            gate = 1;
+                            c = classical_count(V.n, p, h0, h1, &ci, &z, &ccont);
+                        } else {
+                            c = gated_count(law, theta_of(h0), theta_of(h1), relaxed, &gate, &ci, &z, &ccont);
+                        }
+                        if (M.lod_blend == 1) c = V.w * c;
                         C = C + V.sv[j].u * vw[k] * c;
                         if (tr && tr->recs) {
                             const int idx = tr->n++;
@@ -704,6 +802,7 @@ T eval_pixel(const Scene& sc, int px, const Seeds& sd, bool relaxed, Trace* tr) 
                                 R.u = val(V.sv[j].u); R.v = val(vw[k]);
                                 R.x = S.cell.x; R.t = S.cell.t; R.s = val(S.lod.s); R.As = val(As);
                                 R.qx = val(V.qx); R.qy = val(V.qy); R.afx = val(afx); R.afy = val(afy);
+                                R.w = val(V.w);
                             }
                         } else if (tr) {
                             tr->n++;
@@ -740,6 +839,8 @@ int check_material(const OMaterial* m, int nL) {
     if (m->max_sub < 1 || m->max_sub > 64) return -1;
     if (!(m->R > 0.0f && m->R <= 1.0f) || !(m->gamma >= 1e-3f)) return -1;
     if (nL < 0 || nL > 8) return -1;
+    if ((m->lod_blend != 0 && m->lod_blend != 1) || (m->sampler != 0 && m->sampler != 1)) return -1;
+    if (m->rng_table != 0 && m->rng_table != 1) return -1;
     return 0;
 }
 
@@ -850,6 +951,10 @@ void oracle_eval_hash(int32_t i, int32_t j, uint32_t gid, int32_t ax, int32_t ay
     eval_hash(i, j, gid, ax, ay, seed, &h2[0], &h2[1]);
 }
 double oracle_theta(uint32_t h) { return theta_of(h); }
+void oracle_table_words(uint32_t k, uint32_t* h2) { table_words(k, &h2[0], &h2[1]); }
+void oracle_eval_table(int32_t i, int32_t j, uint32_t gid, int32_t ax, int32_t ay, uint32_t seed, uint32_t* h2) {
+    eval_table(i, j, gid, ax, ay, seed, &h2[0], &h2[1]);
+}
 
 double oracle_ndf(int ndf, double ax, double ay, double ht, double hb, double hn) {
     return ndf_D<double>(ndf, ax, ay, ht, hb, hn);
@@ -901,6 +1006,17 @@ void oracle_simplex(double qx, double qy, int32_t* iout, double* wout) {
     simplex_vertices<double>(qx, qy, s);
     for (int k = 0; k < 3; ++k) { iout[2 * k] = s[k].i; iout[2 * k + 1] = s[k].j; wout[k] = s[k].u; }
 }
+
+/* Classical count of one evaluation (words h0, h1).  dout = (z, c_cont); returns c. */
+int oracle_classical_count(double n, double p, uint32_t h0, uint32_t h1, double* dout) {
+    int c; double z, cc;
+    classical_count<double>(n, p, h0, h1, &c, &z, &cc);
+    dout[0] = z; dout[1] = cc;
+    return c;
+}
+
+/* Exact binomial count (inverse CDF) of one evaluation. */
+int oracle_exact_count(int N, double p, double theta) { return exact_binomial_count(N, p, theta); }
 
 /* Gated count of one evaluation.  dout = (P1, mu, sigma, z, c_cont, relaxed); returns c. */
 int oracle_gated_count(double n, double p, double th0, double th1, double* dout) {

@@ -28,7 +28,8 @@ class GlintError(RuntimeError):
 class GlintMaterial(C.Structure):
     _fields_ = [("ndf", C.c_int32), ("alpha_x", C.c_float), ("alpha_y", C.c_float), ("ln_density", C.c_float),
                 ("R", C.c_float), ("F0", C.c_float), ("gamma", C.c_float), ("n_lods", C.c_int32),
-                ("n_rings", C.c_int32), ("lod_factor", C.c_int32), ("max_sub", C.c_int32), ("seed", C.c_uint32)]
+                ("n_rings", C.c_int32), ("lod_factor", C.c_int32), ("max_sub", C.c_int32), ("seed", C.c_uint32),
+                ("lod_blend", C.c_int32), ("sampler", C.c_int32), ("rng_table", C.c_int32)]
 
 
 class GlintLight(C.Structure):
@@ -97,7 +98,8 @@ def check(rc, what):
 def material_struct(m) -> GlintMaterial:
     return GlintMaterial(int(m.ndf), float(m.alpha_x), float(m.alpha_y), float(m.ln_density), float(m.R),
                          float(m.F0), float(m.gamma), int(m.n_lods), int(m.n_rings), int(m.lod_factor),
-                         int(m.max_sub), int(m.seed) & 0xFFFFFFFF)
+                         int(m.max_sub), int(m.seed) & 0xFFFFFFFF, int(getattr(m, "lod_blend", 0)),
+                         int(getattr(m, "sampler", 0)), int(getattr(m, "rng_table", 0)))
 
 
 def lights_struct(lights):

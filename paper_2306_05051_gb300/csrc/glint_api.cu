@@ -24,12 +24,14 @@ const Tables& host_tables() {
             T.d.atan_t[k] = split(std::atan(k / 64.0));
             T.d.log2_t[k] = split(std::log2(1.0 + k / 64.0));
         }
+        for (int j = 0; j < 64; ++j) T.d.exp2_t[j] = split(std::exp2(j / 64.0));
         T.d.pi = split(M_PI);
         T.d.half_pi = split(M_PI / 2);
         T.d.inv_pi = split(1.0 / M_PI);
         T.d.inv_ln2 = split(1.0 / std::log(2.0));
         T.d.inv_sqrt2 = split(1.0 / std::sqrt(2.0));
         T.d.third = split(1.0 / 3.0);
+        T.d.ln2 = split(std::log(2.0));
         const double pre = std::pow(3.0, -0.25);
         const double F2 = 0.5 * (std::sqrt(3.0) - 1.0);
         for (int m = 0; m <= kMaxRings; ++m) {
@@ -64,6 +66,10 @@ int check_material(const GlintMaterial* m) {
     if (!(m->alpha_x > 0.0f) || !(m->alpha_y > 0.0f) || !std::isfinite(m->alpha_x) || !std::isfinite(m->alpha_y))
         return GLINT_ERR_ARG;
     if (!std::isfinite(m->ln_density) || !std::isfinite(m->F0)) return GLINT_ERR_ARG;
+    if ((m->lod_blend != 0 && m->lod_blend != 1) || (m->sampler != 0 && m->sampler != 1)) return GLINT_ERR_ARG;
+    if (m->rng_table != 0 && m->rng_table != 1) return GLINT_ERR_ARG;
+    // the table variant of the image kernels runs the anisotropic grids with the gated sampler
+    if (m->rng_table && (m->sampler || m->n_rings == 0)) return GLINT_ERR_UNSUPPORTED;
     if (std::pow((double)m->lod_factor, m->n_lods - 1) * GLINT_MAX_SUB > 1e30) return GLINT_ERR_ARG;
     return GLINT_OK;
 }
@@ -121,7 +127,7 @@ int num_sms() {
     return g_sm_count[dev];
 }
 
-size_t tables_bytes(int M) { return sizeof(DfTables) + (size_t)rot_entries(M) * sizeof(RotEntry); }
+static_assert(tables_words(kMaxRings) * 4 == sizeof(Tables), "the table copy must reach the last rotation entry");
 
 int make_material_params(const GlintMaterial* m, const GlintLight* lights, int n_lights, KParams* P) {
     const int rc = check_material(m);
@@ -140,6 +146,9 @@ int make_material_params(const GlintMaterial* m, const GlintLight* lights, int n
     P->R = m->R; P->F0 = m->F0; P->gamma = m->gamma;
     P->L = m->n_lods; P->M = m->n_rings; P->f = m->lod_factor; P->Kmax = m->max_sub;
     P->seed = m->seed;
+    P->lod_blend = m->lod_blend;
+    P->sampler = m->sampler;
+    P->rng_table = m->rng_table;
     P->top = (float)std::pow((double)m->lod_factor, m->n_lods - 1);
     P->log2f = m->lod_factor == 4 ? 2 : 1;
     std::memcpy(&P->tables, &host_tables(), sizeof(Tables));

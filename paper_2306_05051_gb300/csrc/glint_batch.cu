@@ -19,7 +19,7 @@ struct GlintContext {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     cudaGraphNode_t kernel_node;
-    bool graph_iso;               // the graph holds the isotropic-grid kernel (n_rings = 0)
+    int graph_variant;            // kernel variant the graph holds (kernel_variant)
     // host copies of the kernel arguments referenced by node updates
     glint::KParams P;
     glint::BatchDesc B;
@@ -110,7 +110,7 @@ cudaError_t capture_graph(GlintContext* c) {
     if (ee != cudaSuccess) return ee;
     if (e != cudaSuccess) return e;
     if ((e = cudaGraphInstantiate(&c->exec, c->graph, 0)) != cudaSuccess) return e;
-    c->graph_iso = c->P.M == 0;
+    c->graph_variant = kernel_variant(c->P);
     size_t nn = 0;
     if ((e = cudaGraphGetNodes(c->graph, nullptr, &nn)) != cudaSuccess) return e;
     cudaGraphNode_t nodes[8];
@@ -131,7 +131,7 @@ cudaError_t update_graph(GlintContext* c) {
     void* args[2] = {&c->P, &c->B};
     cudaKernelNodeParams kp;
     std::memset(&kp, 0, sizeof(kp));
-    kp.func = const_cast<void*>(batch_kernel_fn(c->P.M == 0));
+    kp.func = const_cast<void*>(batch_kernel_fn(kernel_variant(c->P)));
     kp.gridDim = dim3(cfg.blocks);
     kp.blockDim = dim3(cfg.threads);
     kp.sharedMemBytes = (unsigned)fwd_smem_bytes(cfg.threads);
@@ -230,7 +230,7 @@ int glint_eval_batch(GlintContext* c, const GlintFrame* frames, int32_t n_frames
         c->signature = sig;
     }
     fill_batch(c, frames, n_frames, outs, c->launch.threads_per_cta);
-    if (!c->exec || c->graph_iso != (c->P.M == 0)) {      // a new kernel: record again
+    if (!c->exec || c->graph_variant != kernel_variant(c->P)) {      // a new kernel: record again
         if ((rc = cuda_rc(capture_graph(c)))) return rc;
     }
     if ((rc = cuda_rc(update_graph(c)))) return rc;

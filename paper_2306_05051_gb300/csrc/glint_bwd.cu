@@ -154,14 +154,13 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
     float gm[3] = {0.0f, 0.0f, 0.0f};         // alpha_x, alpha_y, ln density
     for (int l = 0; l < F.nL; ++l) {
         LightState L;
-        setup_light<false>(P, F, S, px, l, L);          // no angular texel record needed
+        setup_light<false>(P, T, F, S, px, l, L);       // no angular texel record needed
         if (!L.on) continue;
         LightGrad LG;
         light_grad(P, F, S, px, l, L, LG);
-        CountLaw law[4];
-        for (int i = 0; i < 4; ++i) law[i] = count_law(S.ntr[i], L.p, L.lq);
         float C = 0.0f, Cd = 0.0f, Su = 0.0f, Svx = 0.0f, Svy = 0.0f;
-        float Z0[4] = {0, 0, 0, 0}, Z1[4] = {0, 0, 0, 0};
+        float dC[3] = {0.0f, 0.0f, 0.0f}, dCd[3] = {0.0f, 0.0f, 0.0f};
+        const float p = L.p;
         for (int sub = 0; sub < S.K; ++sub) {
             SubState U;
             // the sub-footprints are the same for every light, so a
@@ -173,8 +172,10 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
                 for (int k = 0; k < ng; ++k) g[k] = 0.0f;
                 return 0.0f;
             }
+#pragma unroll 1
             for (int i = 0; i < 4; ++i) {
                 if (!vertex_used(P.M, i)) continue;
+                const CountLaw law = count_law(S.ntr[i], S.ntr_lo[i], L.p, L.p_lo, L.lq);
                 // the 12 gates of this grid vertex first, then the open ones in
                 // (simplex vertex, texel) order
                 unsigned om = 0u;
@@ -182,8 +183,9 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        om |= gate_open(fmix32(U.S0[3 * i + j] + L.A0[k]), law[i].Tg) ? (1u << (4 * j + k)) : 0u;
+                        om |= gate_open(fmix32(U.S0[3 * i + j] + L.A0[k]), law.Tg) ? (1u << (4 * j + k)) : 0u;
                 float X[3] = {0.0f, 0.0f, 0.0f};
+                float Z0 = 0.0f, Z1 = 0.0f;      // sum of u v and u v z over open, unclamped gates
                 const float u3[3] = {U.uw[3 * i], U.uw[3 * i + 1], U.uw[3 * i + 2]};
                 const uint32_t s13[3] = {U.S1[3 * i], U.S1[3 * i + 1], U.S1[3 * i + 2]};
                 const float fx = LG.fx, fy = LG.fy;
@@ -195,44 +197,44 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
                     const uint32_t a1 = k == 0 ? L.A1[0] : (k == 1 ? L.A1[1] : (k == 2 ? L.A1[2] : L.A1[3]));
                     const float uj = j == 0 ? u3[0] : (j == 1 ? u3[1] : u3[2]);
                     const uint32_t s1 = j == 0 ? s13[0] : (j == 1 ? s13[1] : s13[2]);
-                    const float z = normal_of_word(fmix32(s1 + a1));
-                    const float cc = 1.0f + law[i].mu + law[i].sig * z;
-                    const float ck = fminf(fmaxf(cc, 1.0f), law[i].nceil);
+                    const uint32_t h1 = fmix32(s1 + a1);
+                    const float z = normal_of_word(h1);
+                    float cc;
+                    const float cint = open_count(h1, law.mu, law.mu_lo, law.sig, law.nceil, &cc);
+                    const float ck = fminf(fmaxf(cc, 1.0f), law.nceil);
                     const float xk = vk * ck;
                     X[0] += j == 0 ? xk : 0.0f;
                     X[1] += j == 1 ? xk : 0.0f;
                     X[2] += j == 2 ? xk : 0.0f;
                     C += uj * xk;
-                    Cd += uj * vk * fminf(fmaxf(floorf(cc), 1.0f), law[i].nceil);
+                    Cd += uj * vk * cint;
                     const float axk = k == 0 ? -(1.0f - fy) : (k == 1 ? (1.0f - fy) : (k == 2 ? -fy : fy));
                     const float ayk = k == 0 ? -(1.0f - fx) : (k == 1 ? -fx : (k == 2 ? (1.0f - fx) : fx));
                     Svx += uj * axk * ck;
                     Svy += uj * ayk * ck;
-                    if (cc > 1.0f && cc < law[i].nceil) { Z0[i] += uj * vk; Z1[i] += uj * vk * z; }
+                    if (cc > 1.0f && cc < law.nceil) { Z0 += uj * vk; Z1 += uj * vk * z; }
                 }
                 const float hx = 0.5f * U.qx[i], hy = 0.5f * U.qy[i];
                 Su += U.lower[i] ? hx * (X[1] - X[0]) + hy * (X[2] - X[1]) : hy * (X[1] - X[0]) + hx * (X[2] - X[1]);
+                // d C / d theta through this vertex's count parameters:
+                // d mu = nm1 dp + p dnm1;  d sigma = ((1 - p) d mu - mu dp) / (2 sigma)
+                if (Z0 != 0.0f || Z1 != 0.0f) {
+                    const float n = S.ntr[i];
+                    const float nm1 = n > 1.0f ? n - 1.0f : 0.0f;
+                    const float dnm1 = n > 1.0f ? S.dntr[i] : 0.0f;
+                    const float mu = law.mu, sig = law.sig;
+                    const float is2 = sig > 0.0f ? 0.5f / sig : 0.0f;
+                    auto term = [&](float dp, float dn) {
+                        const float dmu = nm1 * dp + p * dn;
+                        return dmu * Z0 + ((1.0f - p) * dmu - mu * dp) * is2 * Z1;
+                    };
+                    dC[0] += term(LG.dp_da[0], 0.0f);
+                    dC[1] += term(LG.dp_da[1], 0.0f);
+                    dC[2] += term(0.0f, dnm1);
+                    if (LG.dir)
+                        for (int c = 0; c < 3; ++c) dCd[c] += term(LG.dp_dd[c], 0.0f);
+                }
             }
-        }
-        // d C / d theta through the count parameters of each tetrahedron vertex
-        float dC[3] = {0.0f, 0.0f, 0.0f}, dCd[3] = {0.0f, 0.0f, 0.0f};
-        const float p = L.p;
-        for (int i = 0; i < 4; ++i) {
-            const float n = S.ntr[i];
-            const float nm1 = n > 1.0f ? n - 1.0f : 0.0f;
-            const float dnm1 = n > 1.0f ? S.dntr[i] : 0.0f;
-            const float mu = law[i].mu, sig = law[i].sig;
-            // d mu = nm1 dp + p dnm1;  d sigma = ((1 - p) d mu - mu dp) / (2 sigma)
-            auto term = [&](float dp, float dn) {
-                const float dmu = nm1 * dp + p * dn;
-                const float dsig = sig > 0.0f ? ((1.0f - p) * dmu - mu * dp) / (2.0f * sig) : 0.0f;
-                return dmu * Z0[i] + dsig * Z1[i];
-            };
-            dC[0] += term(LG.dp_da[0], 0.0f);
-            dC[1] += term(LG.dp_da[1], 0.0f);
-            dC[2] += term(0.0f, dnm1);
-            if (LG.dir)
-                for (int c = 0; c < 3; ++c) dCd[c] += term(LG.dp_dd[c], 0.0f);
         }
         dC[2] += Su;
         // out_l = shade C / A;  d A / d ln rho = A
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant_
                                                           double* partial, int ng) {
     __shared__ Tables T;
     __shared__ double red[kBwdThreads / 32][kMaxGrad + 1];
-    const int nwords = (int)(sizeof(DfTables) / 4) + rot_entries(P.M) * (int)(sizeof(RotEntry) / 4);
+    const int nwords = tables_words(P.M);
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(&P.tables);
         uint32_t* dst = reinterpret_cast<uint32_t*>(&T);
@@ -355,6 +357,9 @@ int launch_backward(const GlintFrame* frame, const GlintMaterial* material, cons
     int rc = check_frame_shape(frame, lights);
     if (rc) return rc;
     if (frame->mat_px) return GLINT_ERR_UNSUPPORTED;            // gradients of the scalar material only
+    if (!material) return GLINT_ERR_ARG;
+    if (material->lod_blend || material->sampler || material->rng_table)
+        return GLINT_ERR_UNSUPPORTED;                             // ablations: forward only
     KParams P;
     if ((rc = make_material_params(material, lights, frame->n_lights, &P))) return rc;
     if ((rc = check_frame_device(frame, lights))) return rc;

@@ -170,7 +170,8 @@ __device__ __forceinline__ int dffloor_w(df a, float* f, float* g) {
 struct DfTables {
     float2 atan_t[65];     // atan(k / 64), k = 0..64
     float2 log2_t[65];     // log2(1 + k / 64), k = 0..64
-    float2 pi, half_pi, inv_pi, inv_ln2, inv_sqrt2, third;
+    float2 exp2_t[64];     // 2^(j / 64), j = 0..63
+    float2 pi, half_pi, inv_pi, inv_ln2, inv_sqrt2, third, ln2;
 };
 
 __device__ __forceinline__ df ldf(float2 v) { return {v.x, v.y}; }
@@ -189,6 +190,24 @@ __device__ __forceinline__ df dflog2(df x, const DfTables& T) {
         h * h * (-0.5f + h * (0.333333343f + h * (-0.25f + h * (0.2f - h * 0.166666672f)))));
     const df ln1p = d + tail;
     return ln1p * ldf(T.inv_ln2) + ldf(T.log2_t[k]) + (float)(e - 1);
+}
+
+// exp(-x) of a double-float x >= 0 by Tang's table-driven method (ACM TOMS
+// 15(2), 1989): -x log2(e) = m + j/64 + r/ln 2 with |r| <= ln(2)/128, so
+// exp(-x) = 2^m 2^(j/64) exp(r); exp(r) = 1 + r + r^2/2 + ... + r^5/120 with
+// the linear part in double-float (the neglected r^6/720 is below 4e-17).
+// Relative error ~1e-11 over the whole range; 0 where exp(-x) < 2^-125.
+__device__ __forceinline__ df dfexp_neg(df x, const DfTables& T) {
+    if (!(x.hi < 86.0f)) return {0.0f, 0.0f};
+    const df t = -(x * ldf(T.inv_ln2));
+    const int N = __float2int_rn(__fmul_rn(t.hi, 64.0f));
+    const df r = (t - __fmul_rn((float)N, 0.015625f)) * ldf(T.ln2);
+    const float h = r.hi;
+    const float tail = __fmul_rn(__fmul_rn(h, h),
+                                 __fmaf_rn(h, __fmaf_rn(h, __fmaf_rn(h, 8.33333377e-3f, 4.16666679e-2f), 0.166666672f), 0.5f));
+    const df er = (r + tail) + 1.0f;
+    const int j = N & 63, m = N >> 6;
+    return scale2(ldf(T.exp2_t[j]) * er, m);
 }
 
 // atan2 of double-floats: octant reduction, table of atan(k/64) and the

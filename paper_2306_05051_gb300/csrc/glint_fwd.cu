@@ -11,15 +11,55 @@
 // expensive part of the binomial law costs one lane-slot per open gate
 // rather than a warp-slot.  Results are returned to their owner lanes in
 // enqueue order, so the image is deterministic.
+#include <mutex>
 #include "glint_kernels.cuh"
 
 namespace glint {
 
 constexpr int kQ = 64;                    // queue capacity per warp (ring)
 
+// --------------------------------------------------------------------------
+// random-number table (Sec. 6.3, last paragraph; rng_table = 1): 2^16 pairs
+// of words, R[k] = (fmix32(2k G + C), fmix32((2k + 1) G + C)), G = 0x9E3779B9,
+// C = 0x632BE5AB, filled once per device on first use.  An evaluation with
+// spatial word s and angular word a reads R[(s + a) >> 16] in place of the
+// two per-evaluation mixing steps.
+// --------------------------------------------------------------------------
+constexpr int kRngTableBits = 16;
+static __device__ uint2 g_rng_table[1 << kRngTableBits];
+
+__device__ __forceinline__ uint2 rng_table_pair(uint32_t key) {
+    return __ldg(&g_rng_table[key >> (32 - kRngTableBits)]);
+}
+
+__global__ void rng_table_kernel() {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < (1u << kRngTableBits))
+        g_rng_table[k] = make_uint2(fmix32(2u * k * 0x9E3779B9u + 0x632BE5ABu),
+                                    fmix32((2u * k + 1u) * 0x9E3779B9u + 0x632BE5ABu));
+}
+
+// Fill the table once per device: one kernel on `s`, then a wait for it, so
+// that work on any stream may read the table afterwards.
+cudaError_t ensure_rng_table(cudaStream_t s) {
+    static std::mutex mtx;
+    static bool done[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mtx);
+    if (done[dev]) return cudaSuccess;
+    rng_table_kernel<<<(1 << kRngTableBits) / 256, 256, 0, s>>>();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    done[dev] = true;
+    return cudaSuccess;
+}
+
 struct WarpQueue {
     uint32_t word[kQ];                    // pre-image of the second hash word
-    float mu[kQ], sig[kQ], nceil[kQ], w[kQ];
+    float mu[kQ], mu_lo[kQ], sig[kQ], nceil[kQ], w[kQ];
     int32_t owner[kQ];
     float res[32];
     uint32_t mask[32];
@@ -28,7 +68,7 @@ struct WarpQueue {
 // Copy the double-float tables (only the rotation entries up to ring M)
 // from the parameter block into shared memory.
 __device__ __forceinline__ void load_tables(const KParams& P, Tables& T) {
-    const int nwords = (int)(sizeof(DfTables) / 4) + rot_entries(P.M) * (int)(sizeof(RotEntry) / 4);
+    const int nwords = tables_words(P.M);
     const uint32_t* src = reinterpret_cast<const uint32_t*>(&P.tables);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&T);
     for (int k = threadIdx.x; k < nwords; k += blockDim.x) dst[k] = src[k];
@@ -37,6 +77,9 @@ __device__ __forceinline__ void load_tables(const KParams& P, Tables& T) {
 
 // Evaluate the n <= 32 queue entries starting at `head`: lane k takes entry
 // head + k.  Each owner lane then adds its entries' values in queue order.
+// kFinal: the queue holds the second hash word itself (table mode), else
+// its pre-image.
+template <bool kFinal>
 __device__ __noinline__ void flush_queue(WarpQueue& q, int head, int n, float& acc) {
     const int lane = threadIdx.x & 31;
     const int e = (head + lane) & (kQ - 1);
@@ -44,7 +87,8 @@ __device__ __noinline__ void flush_queue(WarpQueue& q, int head, int n, float& a
     int owner = 32 + lane;                       // unique dummy for empty slots
     if (lane < n) {
         float cc;
-        val = q.w[e] * open_count(fmix32(q.word[e]), q.mu[e], q.sig[e], q.nceil[e], &cc);
+        const uint32_t h1 = kFinal ? q.word[e] : fmix32(q.word[e]);
+        val = q.w[e] * open_count(h1, q.mu[e], q.mu_lo[e], q.sig[e], q.nceil[e], &cc);
         owner = q.owner[e];
     }
     q.res[lane] = val;
@@ -64,17 +108,23 @@ __device__ __noinline__ void flush_queue(WarpQueue& q, int head, int n, float& a
 
 struct LightEval {          // what the evaluation loop needs of one light
     bool on;
-    float p, lq, shade;
+    float p, p_lo, lq, shade;
     float v[4];
     uint32_t A0[4], A1[4];
 };
 
 // Shade the pixel of this lane (px valid or not); all 32 lanes call together.
 // ss0 / suw: the CTA's shared arrays of 12 x blockDim spatial words / weights.
-// kIso: isotropic-grid mode (M = 0), tetrahedron vertices 0 and 3 only.
-template <bool kIso>
+// kMode (kernel_variant): kRing the anisotropic grids; kIsoGrid the
+// isotropic-grid mode (M = 0), tetrahedron vertices 0 and 3 only;
+// kClassicalSampler the classical sampler (ablation, sampler = 1), evaluated
+// by each lane for its own pixel (every evaluation draws a count: no gate,
+// no queue), M = 0 handled at run time; kRngTable the uniforms fetched from
+// the random-number table instead of the per-evaluation mixing.
+template <int kMode>
 __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& F, WarpQueue& q, int px,
                             bool valid, uint32_t* ss0, float* suw) {
+    constexpr bool kIso = kMode == kIsoGrid, kClassical = kMode == kClassicalSampler, kTable = kMode == kRngTable;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     PixelSetup S;
@@ -85,7 +135,7 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
     bool any_on = false;
     for (int l = 0; l < F.nL; ++l) {
         ls[l].on = false;
-        if (S.status == 0) setup_light<false>(P, F, S, px, l, ls[l]);
+        if (S.status == 0) setup_light<false>(P, T, F, S, px, l, ls[l]);
         any_on |= ls[l].on;
     }
     // a pixel that no light reaches shades to 0: its sub-footprints are not set up
@@ -102,30 +152,60 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
         SubState U;
         bool act = sub < K && in_range;
         if (act) {
-            in_range = setup_sub<false, kIso>(P, T, S, sub, U, s0s, uws, st);
+            // (the classical variant runs both grid modes: with M = 0 only
+            // vertices 0 and 3 exist, and only the M = 0 rotation entry is loaded)
+            in_range = (kClassical && P.M == 0) ? setup_sub<false, true>(P, T, S, sub, U, s0s, uws, st)
+                                                : setup_sub<false, kIso>(P, T, S, sub, U, s0s, uws, st);
             act = in_range;
         }
 #pragma unroll 1
         for (int l = 0; l < F.nL; ++l) {
             LightEval L;
             L.on = act && ls[l].on;
-            L.p = ls[l].p; L.lq = ls[l].lq; L.shade = ls[l].shade;
+            L.p = ls[l].p; L.p_lo = ls[l].p_lo; L.lq = ls[l].lq; L.shade = ls[l].shade;
 #pragma unroll
             for (int k = 0; k < 4; ++k) { L.v[k] = ls[l].v[k]; L.A0[k] = ls[l].A0[k]; L.A1[k] = ls[l].A1[k]; }
             if (!__any_sync(0xffffffffu, L.on)) continue;
 #pragma unroll 1
             for (int ii = 0; ii < (kIso ? 2 : 4); ++ii) {
                 const int i = kIso ? 3 * ii : ii;
-                CountLaw law = count_law(S.ntr[i], L.p, L.lq);
+                const float shade_i = L.shade * S.wmix[i];        // wmix = 1 unless lod_blend = 1
+                if (kClassical) {
+                    if (!vertex_used(P.M, i) || !L.on) continue;
+                    const ClassicalLaw cl = classical_law(S.ntr[i], S.ntr_lo[i], L.p, L.p_lo);
+#pragma unroll 1
+                    for (int j = 0; j < 3; ++j) {
+                        const uint32_t s0 = s0s[(3 * i + j) * st], s1 = U.S1[3 * i + j];
+                        const float uw = uws[(3 * i + j) * st] * shade_i;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            float cc;
+                            acc += uw * L.v[k] * classical_count(cl, fmix32(s0 + L.A0[k]), fmix32(s1 + L.A1[k]), &cc);
+                        }
+                    }
+                    continue;
+                }
+                CountLaw law = count_law(S.ntr[i], S.ntr_lo[i], L.p, L.p_lo, L.lq);
                 if (!L.on) law.Tg = 0u;
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     const uint32_t s0 = s0s[(3 * i + j) * st], s1 = U.S1[3 * i + j];
-                    const float uw = uws[(3 * i + j) * st] * L.shade;
+                    const float uw = uws[(3 * i + j) * st] * shade_i;
                     // one warp vote for the 4 angular texels: most groups have no open gate
                     bool gk[4];
+                    uint32_t w1[4];                   // table mode: the second words, fetched with the first
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) gk[k] = gate_open(fmix32(s0 + L.A0[k]), law.Tg);
+                    for (int k = 0; k < 4; ++k) {
+                        uint32_t h0;
+                        if (kTable) {
+                            const uint2 t = rng_table_pair(s0 + L.A0[k]);
+                            h0 = t.x; w1[k] = t.y;
+                        } else {
+                            h0 = fmix32(s0 + L.A0[k]);
+                            w1[k] = s1 + L.A1[k];
+                        }
+                        gk[k] = gate_open(h0, law.Tg);
+                    }
                     if (!__any_sync(0xffffffffu, gk[0] | gk[1] | gk[2] | gk[3])) continue;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -134,15 +214,16 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
                         if (m) {
                             if (g) {
                                 const int pos = (head + count + __popc(m & lt_mask)) & (kQ - 1);
-                                q.word[pos] = s1 + L.A1[k];
-                                q.mu[pos] = law.mu; q.sig[pos] = law.sig; q.nceil[pos] = law.nceil;
+                                q.word[pos] = w1[k];
+                                q.mu[pos] = law.mu; q.mu_lo[pos] = law.mu_lo;
+                                q.sig[pos] = law.sig; q.nceil[pos] = law.nceil;
                                 q.w[pos] = uw * L.v[k];
                                 q.owner[pos] = lane;
                             }
                             count += __popc(m);
                             if (count >= 32) {
                                 __syncwarp();
-                                flush_queue(q, head, 32, acc);
+                                flush_queue<kTable>(q, head, 32, acc);
                                 head = (head + 32) & (kQ - 1);
                                 count -= 32;
                             }
@@ -154,7 +235,7 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
     }
     if (count > 0) {
         __syncwarp();
-        flush_queue(q, head, count, acc);
+        flush_queue<kTable>(q, head, count, acc);
     }
     if (S.status != 0 || !in_range) return 0.0f;
     return acc / S.A.hi;
@@ -171,7 +252,7 @@ __device__ __forceinline__ int tile_pixel() {
     return (ln >> 2) * (nw * 4) + w * 4 + (ln & 3);
 }
 
-template <bool kIso>
+template <int kMode>
 __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KParams P, const FrameDesc F) {
     extern __shared__ __align__(16) unsigned char smem[];
     Tables& T = *reinterpret_cast<Tables*>(smem);
@@ -186,7 +267,7 @@ __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KPara
     for (int base = blockIdx.x * blockDim.x; base < F.npx; base += gridDim.x * blockDim.x) {
         __syncthreads();
         const int px = base + tile_pixel();
-        const float o = shade_warp<kIso>(P, T, F, q, px, px < F.npx, ss0, suw);
+        const float o = shade_warp<kMode>(P, T, F, q, px, px < F.npx, ss0, suw);
         if (px < F.npx) __stcs(F.out + px, o);
     }
 }
@@ -195,7 +276,7 @@ __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KPara
 // tile_base[f] <= t < tile_base[f+1].  Persistent: CTAs take tiles from a
 // global counter (reset to 0 before the launch).  Otherwise one CTA per tile
 // (CTA b shades tile b), scheduled by the hardware.
-template <bool kIso>
+template <int kMode>
 __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KParams P,
                                                      const __grid_constant__ BatchDesc B) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -220,7 +301,7 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KPa
         }
         const FrameDesc& F = B.frames[lo];
         const int px = (t - B.tile_base[lo]) * (int)blockDim.x + tile_pixel();
-        const float o = shade_warp<kIso>(P, T, F, q, px, px < F.npx, ss0, suw);
+        const float o = shade_warp<kMode>(P, T, F, q, px, px < F.npx, ss0, suw);
         if (px < F.npx) __stcs(F.out + px, o);
     }
 }
@@ -241,7 +322,7 @@ __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& 
     pr->phi = S.status == 0 ? S.phi.hi : 0.0f; pr->out = 0.0f;
     if (S.status != 0) return;
     LightState ls[kMaxLights];
-    for (int l = 0; l < F.nL; ++l) setup_light<true>(P, F, S, px, l, ls[l]);
+    for (int l = 0; l < F.nL; ++l) setup_light<true>(P, T, F, S, px, l, ls[l]);
     float C[kMaxLights];
     for (int l = 0; l < F.nL; ++l) C[l] = 0.0f;
     int nrec = 0;
@@ -255,17 +336,28 @@ __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& 
             if (!L.on) continue;
             for (int i = 0; i < 4; ++i) {
                 if (!vertex_used(P.M, i)) continue;
-                const CountLaw law = count_law(S.ntr[i], L.p, L.lq);
+                const CountLaw law = count_law(S.ntr[i], S.ntr_lo[i], L.p, L.p_lo, L.lq);
+                const ClassicalLaw cl = classical_law(S.ntr[i], S.ntr_lo[i], L.p, L.p_lo);
                 for (int j = 0; j < 3; ++j) {
                     for (int k = 0; k < 4; ++k) {
-                        const uint32_t h0 = fmix32(U.S0[3 * i + j] + L.A0[k]);
-                        const uint32_t h1 = fmix32(U.S1[3 * i + j] + L.A1[k]);
-                        const bool g = gate_open(h0, law.Tg);
-                        float c = 0.0f, cc = 0.0f;
-                        if (g) {
-                            c = open_count(h1, law.mu, law.sig, law.nceil, &cc);
-                            C[l] += U.uw[3 * i + j] * L.v[k] * c;
+                        uint32_t h0, h1;
+                        if (P.rng_table) {
+                            const uint2 t = rng_table_pair(U.S0[3 * i + j] + L.A0[k]);
+                            h0 = t.x; h1 = t.y;
+                        } else {
+                            h0 = fmix32(U.S0[3 * i + j] + L.A0[k]);
+                            h1 = fmix32(U.S1[3 * i + j] + L.A1[k]);
                         }
+                        bool g;
+                        float c = 0.0f, cc = 0.0f;
+                        if (P.sampler) {
+                            g = true;                             // every evaluation draws a count
+                            c = classical_count(cl, h0, h1, &cc);
+                        } else {
+                            g = gate_open(h0, law.Tg);
+                            if (g) c = open_count(h1, law.mu, law.mu_lo, law.sig, law.nceil, &cc);
+                        }
+                        if (g) C[l] += U.uw[3 * i + j] * L.v[k] * (S.wmix[i] * c);
                         const int idx = (((l * S.K + sub) * 4 + i) * 3 + j) * 4 + k;
                         ++nrec;
                         if (idx < cap) {
@@ -274,7 +366,8 @@ __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& 
                             R.i = U.li[3 * i + j]; R.j = U.lj[3 * i + j]; R.ax = L.ax[k]; R.ay = L.ay[k];
                             R.h0 = h0; R.h1 = h1; R.gate = g ? 1 : 0;
                             R.c = c < 2147483647.0f ? (int)c : 2147483647;
-                            R.n = S.ntr[i]; R.P1 = law.P1; R.mu = law.mu; R.sigma = law.sig; R.c_cont = cc;
+                            R.n = S.ntr[i]; R.P1 = P.sampler ? 1.0f : law.P1;
+                            R.mu = P.sampler ? cl.mu : law.mu; R.sigma = P.sampler ? cl.sig : law.sig; R.c_cont = cc;
                             R.u = U.uw[3 * i + j]; R.v = L.v[k]; R.p = L.p;
                         }
                     }
@@ -305,42 +398,80 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ KPar
     trace_pixel(P, T, F, px, pix + k, recs + (size_t)k * cap, cap);
 }
 
+// Kernel variant of a material (see shade_warp).
+int kernel_variant(const KParams& P) {
+    if (P.sampler) return kClassicalSampler;
+    if (P.rng_table) return kRngTable;
+    return P.M == 0 ? kIsoGrid : kRing;
+}
+
+static const void* fwd_kernel_fn(int v) {
+    switch (v) {
+        case kIsoGrid: return reinterpret_cast<const void*>(&fwd_kernel<kIsoGrid>);
+        case kClassicalSampler: return reinterpret_cast<const void*>(&fwd_kernel<kClassicalSampler>);
+        case kRngTable: return reinterpret_cast<const void*>(&fwd_kernel<kRngTable>);
+        default: return reinterpret_cast<const void*>(&fwd_kernel<kRing>);
+    }
+}
+
+const void* batch_kernel_fn(int v) {
+    switch (v) {
+        case kIsoGrid: return reinterpret_cast<const void*>(&batch_kernel<kIsoGrid>);
+        case kClassicalSampler: return reinterpret_cast<const void*>(&batch_kernel<kClassicalSampler>);
+        case kRngTable: return reinterpret_cast<const void*>(&batch_kernel<kRngTable>);
+        default: return reinterpret_cast<const void*>(&batch_kernel<kRing>);
+    }
+}
+
 static cudaError_t configure_smem() {
     static thread_local int configured_for = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (configured_for == dev) return cudaSuccess;
     const int mx = (int)fwd_smem_bytes(1024);
-    cudaError_t e = cudaFuncSetAttribute(fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
+        e = cudaFuncSetAttribute(fwd_kernel_fn(v), cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel_fn(v), cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    }
     if (e == cudaSuccess) configured_for = dev;
     return e;
 }
 
 cudaError_t launch_fwd(const KParams& P, const FrameDesc& F, cudaStream_t s, FwdLaunch cfg) {
-    const cudaError_t e = configure_smem();
+    cudaError_t e = configure_smem();
+    if (e == cudaSuccess && P.rng_table) e = ensure_rng_table(s);
     if (e != cudaSuccess) return e;
-    if (P.M == 0) fwd_kernel<true><<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, F);
-    else fwd_kernel<false><<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, F);
+    const size_t sm = fwd_smem_bytes(cfg.threads);
+    switch (kernel_variant(P)) {
+        case kIsoGrid: fwd_kernel<kIsoGrid><<<cfg.blocks, cfg.threads, sm, s>>>(P, F); break;
+        case kClassicalSampler: fwd_kernel<kClassicalSampler><<<cfg.blocks, cfg.threads, sm, s>>>(P, F); break;
+        case kRngTable: fwd_kernel<kRngTable><<<cfg.blocks, cfg.threads, sm, s>>>(P, F); break;
+        default: fwd_kernel<kRing><<<cfg.blocks, cfg.threads, sm, s>>>(P, F); break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const KParams& P, const BatchDesc& B, cudaStream_t s, FwdLaunch cfg) {
-    const cudaError_t e = configure_smem();
+    cudaError_t e = configure_smem();
+    if (e == cudaSuccess && P.rng_table) e = ensure_rng_table(s);
     if (e != cudaSuccess) return e;
-    if (P.M == 0) batch_kernel<true><<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, B);
-    else batch_kernel<false><<<cfg.blocks, cfg.threads, fwd_smem_bytes(cfg.threads), s>>>(P, B);
+    const size_t sm = fwd_smem_bytes(cfg.threads);
+    switch (kernel_variant(P)) {
+        case kIsoGrid: batch_kernel<kIsoGrid><<<cfg.blocks, cfg.threads, sm, s>>>(P, B); break;
+        case kClassicalSampler: batch_kernel<kClassicalSampler><<<cfg.blocks, cfg.threads, sm, s>>>(P, B); break;
+        case kRngTable: batch_kernel<kRngTable><<<cfg.blocks, cfg.threads, sm, s>>>(P, B); break;
+        default: batch_kernel<kRing><<<cfg.blocks, cfg.threads, sm, s>>>(P, B); break;
+    }
     return cudaGetLastError();
-}
-
-const void* batch_kernel_fn(bool iso) {
-    return iso ? reinterpret_cast<const void*>(&batch_kernel<true>) : reinterpret_cast<const void*>(&batch_kernel<false>);
 }
 
 cudaError_t launch_trace(const KParams& P, const FrameDesc& F, const int32_t* px, int32_t n_px,
                          GlintTracePix* pix, GlintTraceRec* recs, int32_t cap, cudaStream_t s) {
+    if (P.rng_table) {
+        const cudaError_t e = ensure_rng_table(s);
+        if (e != cudaSuccess) return e;
+    }
     const int threads = 128;
     const int blocks = (n_px + threads - 1) / threads;
     trace_kernel<<<blocks, threads, 0, s>>>(P, F, px, n_px, pix, recs, cap);

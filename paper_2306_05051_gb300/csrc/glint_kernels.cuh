@@ -38,7 +38,14 @@ int cuda_rc(cudaError_t e);
 
 cudaError_t launch_fwd(const KParams& P, const FrameDesc& F, cudaStream_t s, FwdLaunch cfg);
 cudaError_t launch_batch(const KParams& P, const BatchDesc& B, cudaStream_t s, FwdLaunch cfg);
-const void* batch_kernel_fn(bool iso);      // the batch kernel for the isotropic-grid mode or not
+// Image-kernel variants: anisotropic (ring) grids, isotropic-grid mode
+// (n_rings = 0), classical sampler (sampler = 1), random-number table
+// (rng_table = 1), the last three being ablations of the paper's method.
+enum KernelVariant { kRing = 0, kIsoGrid = 1, kClassicalSampler = 2, kRngTable = 3, kNumVariants = 4 };
+int kernel_variant(const KParams& P);
+// Fill the random-number table of the current device on first use (rng_table = 1).
+cudaError_t ensure_rng_table(cudaStream_t s);
+const void* batch_kernel_fn(int variant);   // the batch kernel of a variant
 size_t fwd_smem_bytes(int threads);
 FwdLaunch default_fwd_launch(int npx);
 FwdLaunch make_fwd_launch(int npx, int threads, int ctas_per_sm);

@@ -13,13 +13,15 @@
 //                                                                 (Eq. 4, Eq. 14, Sec. 6.3)
 //   8. D_P = D(n)/R * C / A and the microfacet BRDF              (Eq. 2-3)
 // Steps 1-6 and the angular coordinate run in double-float (see
-// glint_df.cuh); p, the count parameters and the per-evaluation work run in
-// FP32 and 32-bit integers.
+// glint_df.cuh), and so do the count's mean (N - 1) p and 1 + mu + sigma z
+// (p itself where A p > 8); the gate probability, sigma, the normal quantile
+// and the hashing run in FP32 and 32-bit integers.
 //
 // The pieces below are shared by the image kernels (warp-cooperative, see
 // glint_fwd.cu) and the per-thread parity-trace kernel.
 #pragma once
 #include <cuda_runtime.h>
+#include <cstddef>
 #include <cstdint>
 #include "glint_df.cuh"
 
@@ -46,6 +48,12 @@ struct Tables {
     RotEntry rot[kRotEntries];
 };
 
+// 32-bit words of a Tables block up to the rotation entries of ring M (the
+// rotation entries start at their 16-byte aligned offset, after padding)
+__host__ __device__ constexpr int tables_words(int M) {
+    return (int)((offsetof(Tables, rot) + (size_t)rot_entries(M) * sizeof(RotEntry)) / 4);
+}
+
 struct KLight {
     int32_t kind;
     float dx, dy, dz, E;
@@ -70,6 +78,9 @@ struct KParams {
     float R, F0, gamma;
     int32_t L, M, f, Kmax;
     uint32_t seed;
+    int32_t lod_blend;           // 0 distributed binomial (Sec. 4.2); 1 linear mix of LOD outputs (Sec. 3)
+    int32_t sampler;             // 0 gated Gaussian; 1 classical Gaussian / Bernoulli loop (Sec. 6.3)
+    int32_t rng_table;           // 1: uniforms from the precomputed random-number table (Sec. 6.3)
     float top;                   // f^(L-1)
     int32_t log2f;               // log2(f): 1 or 2
     Tables tables;
@@ -116,30 +127,115 @@ __device__ __forceinline__ float normal_of_word(uint32_t h) {
 // --------------------------------------------------------------------------
 struct CountLaw {
     uint32_t Tg;      // gate threshold: theta0 < P>=1  <=>  ((h0 >> 7) | 1) < Tg
-    float P1, mu, sig, nceil;
+    float P1;
+    float mu, mu_lo;  // mu = (N - 1) p in double-float (mu + mu_lo)
+    float sig, nceil;
 };
 
-// lq = log1pf(-p), computed once per pixel and light (setup_light)
-__device__ __forceinline__ CountLaw count_law(float n, float p, float lq) {
+// ceil of a normalised double-float below 2^24
+__device__ __forceinline__ float dfceil(float hi, float lo) {
+    const float c = ceilf(hi);
+    return (c == hi && lo > 0.0f) ? c + 1.0f : c;
+}
+
+// Counts whose mean exceeds this are formed in double-float: below it the
+// FP32 mean (N - 1) p is within ~1e-5 of the exact one (relative errors of N
+// and p of a few 1e-7 times a mean of at most 32).
+constexpr float kDfCountMean = 32.0f;
+
+// Parameters of the gated law for N = n + n_lo trials of success probability
+// p + p_lo (both double-float).  Where N p > kDfCountMean, mu = (N - 1) p is
+// formed in double-float: a count of 10^4 has an FP32 spacing of 1e-3, and
+// every relative error of N or p reaches the count multiplied by mu.  P>=1
+// and sigma keep FP32 (their errors move the gate by ~1e-7 relative and the
+// count by ~sigma 1e-7).  lq = log1pf(-p), computed once per pixel and light
+// (setup_light).
+__device__ __forceinline__ CountLaw count_law(float n, float n_lo, float p, float p_lo, float lq) {
     CountLaw c;
     c.P1 = 0.0f;
     if (n > 0.0f && p > 0.0f) c.P1 = p >= 1.0f ? 1.0f : -expm1f(n * lq);
     c.Tg = (uint32_t)ceilf(c.P1 * 33554432.0f);            // 2^25
-    const float nm1 = n > 1.0f ? n - 1.0f : 0.0f;
-    c.mu = nm1 * p;
+    if (n * p > kDfCountMean) {
+        const df mu = (df{n, n_lo} - 1.0f) * df{p, p_lo};
+        c.mu = mu.hi; c.mu_lo = mu.lo;
+    } else {
+        c.mu = n > 1.0f ? (n - 1.0f) * p : 0.0f;
+        c.mu_lo = 0.0f;
+    }
     const float var = c.mu * (1.0f - p);
     c.sig = var > 0.0f ? sqrtf(var) : 0.0f;
-    c.nceil = ceilf(n);
+    c.nceil = dfceil(n, n_lo);
     return c;
 }
 
 __device__ __forceinline__ bool gate_open(uint32_t h0, uint32_t Tg) { return ((h0 >> 7) | 1u) < Tg; }
 
 // Count of an open gate: one success plus the Gaussian stand-in for
-// b(N-1, p), clamped to [1, ceil N].
-__device__ __forceinline__ float open_count(uint32_t h1, float mu, float sig, float nceil, float* cc) {
-    *cc = 1.0f + mu + sig * normal_of_word(h1);
-    return fminf(fmaxf(floorf(*cc), 1.0f), nceil);
+// b(N-1, p), clamped to [1, ceil N].  1 + mu + sigma z is formed in
+// double-float and floored exactly; *cc receives it rounded to FP32.
+__device__ __forceinline__ float open_count(uint32_t h1, float mu, float mu_lo, float sig, float nceil, float* cc) {
+    const df c = (df{mu, mu_lo} + 1.0f) + sig * normal_of_word(h1);
+    float fl = floorf(c.hi);
+    if (c.hi == fl && c.lo < 0.0f) fl -= 1.0f;              // c.hi - fl is exact and below 1 otherwise
+    *cc = c.hi;
+    return fminf(fmaxf(fl, 1.0f), nceil);
+}
+
+// --------------------------------------------------------------------------
+// classical binomial approximation (Sec. 6.3, the sampler the paper
+// replaces; the ablation sampler = 1)
+// --------------------------------------------------------------------------
+constexpr int kClassicalLoopMax = 16;
+
+struct ClassicalLaw {
+    bool gauss;       // floored Gaussian (N p > 5 or N > 16), else the Bernoulli loop
+    float mu, mu_lo;  // N p (Gaussian branch, double-float where large)
+    float sig;        // sqrt(N p (1 - p))
+    float nceil;
+    int nt;           // loop: ceil N trials
+    uint32_t T, T_last;   // loop: success thresholds (((w >> 7) | 1) < T  <=>  theta < p)
+};
+
+__device__ __forceinline__ ClassicalLaw classical_law(float n, float n_lo, float p, float p_lo) {
+    ClassicalLaw c;
+    c.nceil = dfceil(n, n_lo);
+    c.nt = 0;
+    c.gauss = false;
+    c.mu = c.mu_lo = c.sig = 0.0f;
+    c.T = c.T_last = 0u;
+    if (!(n > 0.0f) || !(p > 0.0f)) return c;
+    const df np = df{n, n_lo} * df{p, p_lo};
+    c.gauss = dflt(mkdf(5.0f), np) || dflt(mkdf((float)kClassicalLoopMax), df{n, n_lo});
+    if (c.gauss) {
+        c.mu = np.hi; c.mu_lo = np.lo;
+        const float var = np.hi * (1.0f - p);
+        c.sig = var > 0.0f ? sqrtf(var) : 0.0f;
+    } else {
+        c.nt = (int)c.nceil;
+        const float fr = __fadd_rn(__fsub_rn(n, floorf(n)), n_lo);      // weight of a fractional last trial
+        c.T = (uint32_t)ceilf(p * 33554432.0f);                          // 2^25
+        c.T_last = fr > 0.0f ? (uint32_t)ceilf(p * fr * 33554432.0f) : c.T;
+    }
+    return c;
+}
+
+// Count of one evaluation with words h0, h1; *cc receives the Gaussian's
+// value (or the loop count plus 1/2).
+__device__ __forceinline__ float classical_count(const ClassicalLaw& L, uint32_t h0, uint32_t h1, float* cc) {
+    if (L.gauss) {
+        const df c = df{L.mu, L.mu_lo} + L.sig * normal_of_word(h0);
+        float fl = floorf(c.hi);
+        if (c.hi == fl && c.lo < 0.0f) fl -= 1.0f;
+        *cc = c.hi;
+        return fminf(fmaxf(fl, 0.0f), L.nceil);
+    }
+    float c = 0.0f;
+    for (int k = 1; k <= L.nt; ++k) {
+        const uint32_t w = fmix32(h1 + (uint32_t)k * 0x9E3779B9u);
+        c += ((w >> 7) | 1u) < (k == L.nt ? L.T_last : L.T) ? 1.0f : 0.0f;
+    }
+    *cc = c + 0.5f;
+    return c;
 }
 
 // --------------------------------------------------------------------------
@@ -175,6 +271,8 @@ struct PixelSetup {
     df sig0, sig1, u0x, u0y;
     Vert vert[4];
     float ntr[4];       // trials of the 4 tetrahedron vertices (per sub-footprint)
+    float ntr_lo[4];    // their low words (double-float trials)
+    float wmix[4];      // linear mix (lod_blend = 1): LOD weight of each vertex's count; else 1
     float dntr[4];      // d ntr / d ln(density) (adjoint)
     df srho;
     // shading frame and view direction (local frame), for the lights
@@ -380,7 +478,19 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
         S.vert[i].kor = k == 0 ? k0 : (k == 1 ? k1 : k2);
         S.vert[i].level = level + (i >= 3 - c ? 1 : 0);
         const df ni = pinned ? w[i] * As : scale2(w[i], S.vert[i].level * P.log2f);
-        S.ntr[i] = ni.hi;
+        if (P.lod_blend) {
+            // linear mix of LOD outputs (Sec. 3): each vertex counts over its
+            // whole cell (f^level flakes; pinned: A_s) and its count is
+            // weighted by w_i afterwards
+            const df nf = pinned ? As : mkdf(pow2f(S.vert[i].level * P.log2f));
+            S.ntr[i] = nf.hi;
+            S.ntr_lo[i] = nf.lo;
+            S.wmix[i] = __fadd_rn(w[i].hi, w[i].lo);
+        } else {
+            S.ntr[i] = ni.hi;
+            S.ntr_lo[i] = ni.lo;
+            S.wmix[i] = 1.0f;
+        }
         if (kTrace) {
             const float dw = i == 0 ? -ds : (i == 3 ? ds : 0.0f);
             S.dntr[i] = pinned ? ni.hi : dw * pow2f((S.vert[i].level) * P.log2f);
@@ -395,6 +505,7 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
 struct LightState {
     bool on;
     float p, shade;               // p of Eq. 4; F G D(n) E / (4 R cos_v)
+    float p_lo;                   // low word of p (double-float where the counts can be large)
     float lq;                     // log(1 - p) (count laws)
     float v[4];                   // angular bilinear weights
     uint32_t A0[4], A1[4];        // angular hash words
@@ -404,8 +515,8 @@ struct LightState {
 // kTrace: also record the angular texels (ax, ay) for the trace and adjoint
 // kernels; the image kernels skip those stores.
 template <bool kTrace>
-static __device__ __forceinline__ void setup_light(const KParams& P, const FrameDesc& F, const PixelSetup& S, int px,
-                                               int l, LightState& L) {
+static __device__ __forceinline__ void setup_light(const KParams& P, const Tables& T, const FrameDesc& F,
+                                                   const PixelSetup& S, int px, int l, LightState& L) {
     L.on = false;
     const KLight kl = P.lights[l];
     float lr[3], E;
@@ -438,6 +549,26 @@ static __device__ __forceinline__ void setup_light(const KParams& P, const Frame
     const float hn2 = hn * hn;
     const float rat = P.ndf == 0 ? expf(-e / hn2) / (hn2 * hn2) : 1.0f / ((e + hn2) * (e + hn2));
     L.p = fminf(P.R * rat, 1.0f);
+    L.p_lo = 0.0f;
+    // Where the counts can be large (A p > kDfCountMean: mu = (N - 1) p
+    // reaches the count, and p's FP32 relative error of up to a few 1e-6
+    // would move it by more than the count tolerance) p is formed again in
+    // double-float from the double-float half-vector.
+    if (L.p < 1.0f && S.A.hi * L.p > kDfCountMean) {
+        const df tx = div_by(h[0], S.ax, approx_rcp(S.ax)), ty = div_by(h[1], S.ay, approx_rcp(S.ay));
+        const df ed = tx * tx + ty * ty;
+        const df hn2d = h[2] * h[2];
+        df rd;
+        if (P.ndf == 0) {
+            rd = dfexp_neg(ed / hn2d, T.d) / (hn2d * hn2d);
+        } else {
+            const df dd = ed + hn2d;
+            rd = 1.0f / (dd * dd);
+        }
+        df pd = rd * P.R;
+        if (!dflt(pd, 1.0f)) pd = mkdf(1.0f);
+        L.p = pd.hi; L.p_lo = pd.lo;
+    }
     L.lq = log1pf(-L.p);
     // Eq. 14: bilinear angular texels of the projected half-vector; the
     // weights are formed from double-float fractions so each keeps full

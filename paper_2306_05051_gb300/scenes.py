@@ -45,6 +45,9 @@ class Material:
     lod_factor: int = 4
     max_sub: int = 64
     seed: int = DEFAULT_SEED
+    lod_blend: int = 0             # 0 distributed binomial (Sec. 4.2); 1 linear mix of LOD outputs (Sec. 3)
+    sampler: int = 0               # 0 gated Gaussian (Sec. 6.3); 1 classical Gaussian / Bernoulli loop
+    rng_table: int = 0             # 0 hashed uniforms; 1 uniforms fetched from a precomputed table (Sec. 6.3)
 
 
 @dataclass

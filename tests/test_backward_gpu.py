@@ -39,6 +39,20 @@ def test_adjoint_matches_oracle_dual_gradient(orc, fit):
         assert abs(g[k] - g6[k]) <= 1e-3 * abs(g6[k]) + 1e-6 * np.abs(g6).max(), (NAMES[k], g[k], g6[k])
 
 
+def test_adjoint_with_fresnel_f0_matches_oracle(orc, fit):
+    """F0 = 0.04: the Schlick term and its derivative through the half-vector
+    (light direction) enter the gradient."""
+    import dataclasses
+    sc, scd, go = fit
+    mat = dataclasses.replace(sc.material, F0=0.04)
+    g = glint.backward(scd, go, material=mat).cpu().numpy().astype(np.float64)
+    g6, _, _ = orc.grad(sc, go.cpu().numpy().astype(np.float64).reshape(-1), material=mat)
+    g1, _, _ = orc.grad(sc, go.cpu().numpy().astype(np.float64).reshape(-1))
+    assert np.abs(g6[3:] - g1[3:]).max() > 1e-3 * np.abs(g1[3:]).max()     # F changes the direction gradient
+    for k in range(6):
+        assert abs(g[k] - g6[k]) <= 1e-3 * abs(g6[k]) + 1e-6 * np.abs(g6).max(), (NAMES[k], g[k], g6[k])
+
+
 def test_relaxed_image_matches_oracle(orc, fit):
     sc, scd, go = fit
     _, rel = glint.backward(scd, go, relaxed=True)

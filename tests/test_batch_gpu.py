@@ -48,6 +48,32 @@ def test_batch_matches_oracle_on_sampled_pixels(orc):
         parity.check_image(orc, sc, s, img, ref, px=px, sample_trace=60)
 
 
+def test_batch_orbit_64_frames_at_full_size(orc):
+    """The benchmarked batch: 64 orbit frames, 16 each of 256^2, 512^2,
+    1280x720 and 1920x1080, in one tuned, graph-replayed launch.  Every frame
+    equals its glint_eval image bit for bit, and two 1920x1080 frames match
+    the oracle on sampled pixels."""
+    fr = scenes.orbit_frames(64, device=DEV)
+    assert sorted({(s.width, s.height) for s in fr}) == [(256, 256), (512, 512), (1280, 720), (1920, 1080)]
+    ctx = glint.BatchContext(DEV)
+    outs = ctx.render(fr)
+    outs = ctx.render(fr)                          # graph replay
+    torch.cuda.synchronize()
+    for s, o in zip(fr, outs):
+        assert torch.equal(o, glint.render_scene(s)), s.name
+    ctx.close()
+    rng = np.random.default_rng(9)
+    big = [k for k, s in enumerate(fr) if s.width == 1920][:2]
+    for k in big:
+        s = fr[k]
+        sc = s.to("cpu")
+        fg = np.flatnonzero(sc.gbuf[..., 6:9].abs().sum(-1).reshape(-1).numpy() > 0)
+        px = np.sort(rng.choice(fg, 6000, replace=False)).astype(np.int32)
+        ref = orc.eval_image(sc, px=px)
+        img = outs[k].cpu().numpy().astype(np.float64)
+        parity.check_image(orc, sc, s, img, ref, px=px, sample_trace=300)
+
+
 def test_batch_fixed_launch_shapes_and_reuse():
     fr = _frames(6)
     ref = [glint.render_scene(s) for s in fr]

@@ -22,8 +22,7 @@ def _render(scene_dev):
 
 
 def _summary(name, s):
-    print(f"[{name}] traced records {s['n_rec']}, excused mismatches {s['n_excused']} "
-          f"(FP32-undecidable counts {s['n_fp32_undecided']}), "
+    print(f"[{name}] traced pixels {s['n_traced']}, records {s['n_rec']}, excused mismatches {s['n_excused']}, "
           f"pixels over tol {s['over']}, max rel err (matched) {s['max_err_matched']:.3g}")
 
 
@@ -35,6 +34,42 @@ def test_plane45_full_image(orc, ndf):
     assert np.count_nonzero(ref) > 1000
     s = parity.check_image(orc, sc, sc.to(DEV), img, ref, sample_trace=600)
     _summary(f"plane45 ndf={ndf}", s)
+
+
+@pytest.mark.parametrize("which", ["plane45", "plane45_ggx", "grazing_plane"])
+def test_fresnel_f0(orc, which):
+    """Schlick F with F0 = 0.04 (a dielectric), so that the Fresnel term is
+    not identically 1: the 45 degree plane (view and light near the normal,
+    F just above F0) and the grazing plane (F up to several times F0)."""
+    import dataclasses
+    base = {"plane45": lambda: scenes.plane45(ndf=0), "plane45_ggx": lambda: scenes.plane45(ndf=1),
+            "grazing_plane": lambda: scenes.grazing_plane(480, 270)}[which]()
+    sc = dataclasses.replace(base, material=dataclasses.replace(base.material, F0=0.04))
+    img = _render(sc.to(DEV))
+    ref = orc.eval_image(sc)
+    one = orc.eval_image(base)
+    lit = one != 0
+    ratio = ref[lit] / one[lit]
+    f0 = float(np.float32(0.04))
+    assert ratio.min() >= f0 - 1e-12 and ratio.max() < 1.0 and ratio.max() > f0 * (1 + 1e-4)
+    if which == "grazing_plane":
+        assert ratio.max() > 2 * f0
+    s = parity.check_image(orc, sc, sc.to(DEV), img, ref, sample_trace=600)
+    _summary(f"{which} F0=0.04", s)
+
+
+@pytest.mark.parametrize("gamma", [0.01, 0.2])
+@pytest.mark.parametrize("which", ["plane45", "sphere_plane"])
+def test_angular_texel_size(orc, which, gamma):
+    """The angular grid at a finer (0.01) and a coarser (0.2) texel than the
+    default 0.05: the angular coordinate h / gamma and its floor."""
+    import dataclasses
+    sc = scenes.plane45() if which == "plane45" else scenes.sphere_plane(480, 270)
+    sc = dataclasses.replace(sc, material=dataclasses.replace(sc.material, gamma=gamma))
+    img = _render(sc.to(DEV))
+    ref = orc.eval_image(sc)
+    s = parity.check_image(orc, sc, sc.to(DEV), img, ref, sample_trace=400)
+    _summary(f"{which} gamma={gamma}", s)
 
 
 def test_plane_sphere_fit_full_image(orc):

@@ -3,11 +3,11 @@ allocate device memory (a renderer with a fixed memory budget, code that
 must not synchronise the device mid-frame, a plug-in whose host owns every
 allocation).  Its tile counters live in a static device array instead of
 memory from cudaMalloc.  Called through the C ABI, twice in a row, it must
-give the same images as glint_eval.  This file is collected last so that a
-run stopping at the first failure has already run every other test."""
+give glint_eval's images bit for bit (the batch kernel gives the same bits
+for every launch shape).  This file is collected last so that a run stopping
+at the first failure has already run every other test."""
 import ctypes as C
 
-import numpy as np
 import pytest
 import torch
 
@@ -15,8 +15,6 @@ from paper_2306_05051_gb300 import _lib, glint, scenes
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-RAD_TOL = 1e-4           # relative radiance tolerance used by the parity tests
-
 
 def _call(frames, outs, stream=None):
     n = len(frames)
@@ -31,13 +29,6 @@ def _call(frames, outs, stream=None):
         return _lib.lib().glint_eval_batch_noalloc(arr, n, C.byref(mat), lts, optr, int(s.cuda_stream))
 
 
-def _close(a, b):
-    a = a.cpu().numpy().astype(np.float64)
-    b = b.cpu().numpy().astype(np.float64)
-    scale = max(np.abs(b).mean(), 1e-30)
-    return np.all(np.abs(a - b) <= RAD_TOL * np.maximum(np.abs(b), 1e-6 * scale))
-
-
 def test_noalloc_batch_matches_glint_eval_on_two_calls():
     # 130 frames: two launches (128 + 2), i.e. two counters of the static array
     res = [(16, 16), (24, 8), (40, 30), (7, 5), (64, 36)]
@@ -49,7 +40,7 @@ def test_noalloc_batch_matches_glint_eval_on_two_calls():
         assert _call(frames, outs) == 0
         torch.cuda.synchronize()
         for f, o, r in zip(frames, outs, refs):
-            assert _close(o, r), (call, f.name)
+            assert torch.equal(o, r), (call, f.name)
 
 
 def test_noalloc_batch_larger_frames_and_side_stream():
@@ -62,7 +53,7 @@ def test_noalloc_batch_larger_frames_and_side_stream():
         assert _call(frames, outs, stream=s) == 0
         s.synchronize()
         for o, r in zip(outs, refs):
-            assert _close(o, r)
+            assert torch.equal(o, r)
 
 
 def test_noalloc_rejects_batches_beyond_the_static_scratch():
