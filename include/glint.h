@@ -290,6 +290,66 @@ int glint_eval_batch_noalloc(const GlintFrame* frames, int32_t n_frames,
                              const GlintMaterial* material, const GlintLight* lights,
                              float* const* outs, void* stream);
 
+/* Synthetic G-buffers generated on the GPU: the analytic ray casts that make
+ * the benchmark inputs (the paper's Sec. 7.1 scenes are Unity assets; these
+ * are seeded stand-ins of the same kind).  The paper has no counterpart: the
+ * glint shader reads a G-buffer that a renderer already rasterised.  One
+ * thread per pixel in FP64, each output rounded once to float, matching the
+ * package's seeded CPU generator (scenes.py) up to the rounding of a few
+ * ulps of FP64 (different sin/atan2 implementations and summation order).
+ * Layouts as GlintFrame; all output pointers device, 16-byte aligned
+ * (mat_px 8-byte); asynchronous on `stream`.
+ *
+ * Camera: pinhole at eye with orthonormal basis (fwd, right, up) and
+ * vertical half-angle atan(tan_half_fov); pixel (x, y) looks along
+ * fwd + sx right + sy up, sx = ((x + 0.5) 2/W - 1) tan_half_fov W/H,
+ * sy = (1 - (y + 0.5) 2/H) tan_half_fov; uv derivatives by first-order ray
+ * differentials (Igehy 1999). */
+#define GLINT_MAX_WAVES 32
+
+typedef struct GlintCamera {
+    double eye[3];
+    double fwd[3], right[3], up[3];
+    double tan_half_fov;
+    int32_t width, height;
+} GlintCamera;
+
+/* Heightfield y = sum_k amp[k] sin(kx[k] x + kz[k] z + phase[k]), n_waves <=
+ * GLINT_MAX_WAVES, hit by marching the slab |y| <= sum amp in n_march even
+ * steps to the first sign change of y - h and bisecting that bracket
+ * n_bisect times.  uv = uv_scale (x, z) wrapped to [0, uv_scale); normal and
+ * tangent (direction of increasing u) of the heightfield; view direction
+ * -D/|D|.  Every ray must point below the horizon and the eye must lie
+ * above the slab (else GLINT_ERR_ARG).  The whole frame is written. */
+typedef struct GlintHeightfield {
+    int32_t n_waves, n_march, n_bisect, pad;
+    double kx[GLINT_MAX_WAVES], kz[GLINT_MAX_WAVES], phase[GLINT_MAX_WAVES], amp[GLINT_MAX_WAVES];
+    double uv_scale;
+} GlintHeightfield;
+int glint_gbuffer_heightfield(const GlintCamera* camera, const GlintHeightfield* field, float* gbuf, void* stream);
+
+/* Sphere (center, radius; uv = sphere_uv_scale (atan2(z, x)/(2 pi) + 1/2,
+ * acos(y/r)/pi), tangent along increasing azimuth) on the ground plane y = 0
+ * bounded by |x|, |z| <= plane_half_extent (uv = plane_uv_scale (x, z)
+ * wrapped to [0, plane_uv_wrap), tangent +x); n_lights point lights (per
+ * pixel: direction to the light and E = I / d^2 into light_px); material
+ * plane (alpha, 10^log10 density) by bilinear value noise over two
+ * [noise_h][noise_w] device grids of doubles, one value every noise_cell
+ * pixels (pixel (x, y) at ((x + 0.5)/cell, (y + 0.5)/cell) of the grid).
+ * Pixels that hit nothing are 0 in every plane. */
+typedef struct GlintSpherePlane {
+    double center[3];
+    double radius, sphere_uv_scale;
+    double plane_half_extent, plane_uv_scale, plane_uv_wrap;
+    int32_t n_lights, noise_cell, noise_w, noise_h;
+    double light_pos[GLINT_MAX_LIGHTS][3];
+    double light_I[GLINT_MAX_LIGHTS];
+    const double* noise_alpha;
+    const double* noise_log10_density;
+} GlintSpherePlane;
+int glint_gbuffer_sphere_plane(const GlintCamera* camera, const GlintSpherePlane* scene, float* gbuf,
+                               float* light_px, float* mat_px, void* stream);
+
 /* Parity trace of selected pixels: for each listed pixel, a summary and the
  * records of every binomial evaluation in the canonical order (light,
  * sub-footprint, tetrahedron vertex 0..3, simplex vertex 0..2, angular

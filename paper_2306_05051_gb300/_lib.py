@@ -40,6 +40,28 @@ class GlintLaunch(C.Structure):
     _fields_ = [("threads_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32)]
 
 
+MAX_WAVES = 32
+
+
+class GlintCamera(C.Structure):
+    _fields_ = [("eye", C.c_double * 3), ("fwd", C.c_double * 3), ("right", C.c_double * 3), ("up", C.c_double * 3),
+                ("tan_half_fov", C.c_double), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class GlintHeightfield(C.Structure):
+    _fields_ = [("n_waves", C.c_int32), ("n_march", C.c_int32), ("n_bisect", C.c_int32), ("pad", C.c_int32),
+                ("kx", C.c_double * MAX_WAVES), ("kz", C.c_double * MAX_WAVES), ("phase", C.c_double * MAX_WAVES),
+                ("amp", C.c_double * MAX_WAVES), ("uv_scale", C.c_double)]
+
+
+class GlintSpherePlane(C.Structure):
+    _fields_ = [("center", C.c_double * 3), ("radius", C.c_double), ("sphere_uv_scale", C.c_double),
+                ("plane_half_extent", C.c_double), ("plane_uv_scale", C.c_double), ("plane_uv_wrap", C.c_double),
+                ("n_lights", C.c_int32), ("noise_cell", C.c_int32), ("noise_w", C.c_int32), ("noise_h", C.c_int32),
+                ("light_pos", (C.c_double * 3) * 8), ("light_I", C.c_double * 8),
+                ("noise_alpha", C.c_void_p), ("noise_log10_density", C.c_void_p)]
+
+
 class GlintFrame(C.Structure):
     _fields_ = [("gbuf", C.c_void_p), ("light_px", C.c_void_p), ("mat_px", C.c_void_p),
                 ("width", C.c_int32), ("height", C.c_int32), ("n_lights", C.c_int32)]
@@ -72,6 +94,8 @@ SIGNATURES = {
     "glint_backward_workspace_size": (C.c_size_t, [_P]),
     "glint_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "glint_fit_l2": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "glint_gbuffer_heightfield": (C.c_int, [_P, _P, _P, _P]),
+    "glint_gbuffer_sphere_plane": (C.c_int, [_P, _P, _P, _P, _P, _P]),
 }
 
 

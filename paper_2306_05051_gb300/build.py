@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libglint.so")
-SOURCES = ["glint_api.cu", "glint_fwd.cu", "glint_batch.cu", "glint_noalloc.cu", "glint_bwd.cu"]
+SOURCES = ["glint_api.cu", "glint_fwd.cu", "glint_batch.cu", "glint_noalloc.cu", "glint_bwd.cu", "glint_gbuffer.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

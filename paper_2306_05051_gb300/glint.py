@@ -273,3 +273,74 @@ class GlintBRDF(torch.autograd.Function):
         ga = g[:3].to(device=adev, dtype=adt)
         gd = g[3:].reshape(-1, 3).to(device=ddev, dtype=ddt)
         return ga[0], ga[1], ga[2], gd, None
+
+
+# --------------------------------------------------------------------------
+# synthetic G-buffers generated on the GPU (glint_gbuffer_*)
+# --------------------------------------------------------------------------
+def _camera_struct(cam, tan_half_fov, W, H):
+    eye, fwd, right, up = (t.detach().cpu().double().tolist() for t in cam)
+    return _lib.GlintCamera((C.c_double * 3)(*eye), (C.c_double * 3)(*fwd), (C.c_double * 3)(*right),
+                            (C.c_double * 3)(*up), float(tan_half_fov), int(W), int(H))
+
+
+def gbuffer_heightmap(W=1920, H=1080, view_deg=25.0, seed=5, alpha=1.0, density=1e7, rms_slope=0.45,
+                      device="cuda", n_march=128, n_bisect=48, stream=None) -> Scene:
+    """The heightmap (rms_slope > 0) or plane (rms_slope = 0) view of
+    scenes.heightmap, ray-marched by glint_gbuffer_heightfield on the GPU."""
+    import math
+    from . import scenes
+    eye, target, up = scenes.heightmap_camera(view_deg)
+    cam = _camera_struct(scenes.camera_basis(eye, target, up), math.tan(math.radians(30.0) / 2), W, H)
+    hf = scenes.Heightfield.seeded(seed, rms_slope=rms_slope)
+    n = int(hf.kx.numel())
+    if n > _lib.MAX_WAVES:
+        raise ValueError("too many waves")
+    f = _lib.GlintHeightfield()
+    f.n_waves, f.n_march, f.n_bisect = n, int(n_march), int(n_bisect)
+    for k in range(n):
+        f.kx[k], f.kz[k] = float(hf.kx[k]), float(hf.kz[k])
+        f.phase[k], f.amp[k] = float(hf.phase[k]), float(hf.amp[k])
+    f.uv_scale = 64.0
+    dev = torch.device(device)
+    gbuf = torch.empty(H, W, 16, dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        rc = _lib.lib().glint_gbuffer_heightfield(C.byref(cam), C.byref(f), gbuf.data_ptr(), _stream_handle(stream))
+    _lib.check(rc, "glint_gbuffer_heightfield")
+    name = "heightmap" if rms_slope > 0 else "plane"
+    return Scene(f"{name}{int(round(view_deg))}", gbuf, None, None, scenes.heightmap_material(alpha, density),
+                 [Light(kind=1, dir=scenes.HEIGHTMAP_LIGHT_DIR, intensity=1.0)])
+
+
+def gbuffer_sphere_plane(W=3840, H=2160, azimuth_deg=0.0, seed=3, device="cuda", stream=None) -> Scene:
+    """The frame of scenes.sphere_plane, ray-cast by glint_gbuffer_sphere_plane
+    on the GPU (the value-noise lattices are drawn on the host from the same
+    seeded generator)."""
+    from . import scenes
+    st = scenes.sphere_plane_setup(W, H, azimuth_deg, seed)
+    dev = torch.device(device)
+    cam = _camera_struct(st["camera"], st["tan_half_fov"], W, H)
+    na = st["noise_alpha"].to(dev).contiguous()
+    nr = st["noise_log10_density"].to(dev).contiguous()
+    sp = _lib.GlintSpherePlane()
+    for k in range(3):
+        sp.center[k] = st["center"][k]
+    sp.radius, sp.sphere_uv_scale = st["radius"], st["sphere_uv_scale"]
+    sp.plane_half_extent, sp.plane_uv_scale, sp.plane_uv_wrap = (st["plane_half_extent"], st["plane_uv_scale"],
+                                                                 st["plane_uv_wrap"])
+    sp.n_lights, sp.noise_cell = len(st["light_pos"]), st["noise_cell"]
+    sp.noise_h, sp.noise_w = int(na.shape[0]), int(na.shape[1])
+    for l, (pos, I) in enumerate(zip(st["light_pos"], st["light_I"])):
+        for k in range(3):
+            sp.light_pos[l][k] = pos[k]
+        sp.light_I[l] = I
+    sp.noise_alpha, sp.noise_log10_density = na.data_ptr(), nr.data_ptr()
+    gbuf = torch.empty(H, W, 16, dtype=torch.float32, device=dev)
+    light_px = torch.empty(len(st["light_pos"]), H, W, 4, dtype=torch.float32, device=dev)
+    mat_px = torch.empty(H, W, 2, dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        rc = _lib.lib().glint_gbuffer_sphere_plane(C.byref(cam), C.byref(sp), gbuf.data_ptr(), light_px.data_ptr(),
+                                                   mat_px.data_ptr(), _stream_handle(stream))
+    _lib.check(rc, "glint_gbuffer_sphere_plane")
+    torch.cuda.current_stream(dev).synchronize() if stream is None else stream.synchronize()
+    return Scene("sphere_plane", gbuf, light_px, mat_px, st["material"], st["lights"])

@@ -86,17 +86,25 @@ def _normalize(v: torch.Tensor) -> torch.Tensor:
     return v / torch.linalg.vector_norm(v, dim=-1, keepdim=True).clamp_min(1e-300)
 
 
-def camera_rays(W, H, eye, target, fov_deg=60.0, device="cpu", up=(0.0, 1.0, 0.0)):
-    """Pinhole camera, vertical field of view fov_deg, `up` the world
-    direction that appears upwards on screen.  Returns eye [3],
-    unnormalised directions D [H, W, 3] and their screen derivatives
-    dD/dx, dD/dy [3] (constant for a pinhole)."""
+def camera_basis(eye, target, up=(0.0, 1.0, 0.0), device="cpu"):
+    """(eye, fwd, right, up) of a pinhole camera looking at target, `up` the
+    world direction that appears upwards on screen (float64 tensors)."""
     f64 = torch.float64
     eye = torch.tensor(eye, dtype=f64, device=device)
     fwd = _normalize(torch.tensor(target, dtype=f64, device=device) - eye)
     up0 = torch.tensor(up, dtype=f64, device=device)
     right = _normalize(torch.linalg.cross(fwd, up0))
     up = torch.linalg.cross(right, fwd)
+    return eye, fwd, right, up
+
+
+def camera_rays(W, H, eye, target, fov_deg=60.0, device="cpu", up=(0.0, 1.0, 0.0)):
+    """Pinhole camera, vertical field of view fov_deg, `up` the world
+    direction that appears upwards on screen.  Returns eye [3],
+    unnormalised directions D [H, W, 3] and their screen derivatives
+    dD/dx, dD/dy [3] (constant for a pinhole)."""
+    f64 = torch.float64
+    eye, fwd, right, up = camera_basis(eye, target, up, device)
     th = math.tan(math.radians(fov_deg) / 2)
     aspect = W / H
     xs = (torch.arange(W, dtype=f64, device=device) + 0.5) * (2.0 / W) - 1.0
@@ -145,10 +153,15 @@ def _pack(u, v, dudx, dvdx, dudy, dvdy, n, tg, wv, mask):
     return g
 
 
+def _noise_grid(H, W, cell, gen, lo, hi, device):
+    """The value-noise lattice: uniform values in [lo, hi) every `cell` pixels."""
+    gh, gw = H // cell + 2, W // cell + 2
+    return torch.rand(gh, gw, generator=gen, dtype=torch.float64).to(device) * (hi - lo) + lo
+
+
 def _value_noise(H, W, cell, gen, lo, hi, device):
     """Bilinear value noise: uniform values on a grid every `cell` pixels."""
-    gh, gw = H // cell + 2, W // cell + 2
-    grid = torch.rand(gh, gw, generator=gen, dtype=torch.float64).to(device) * (hi - lo) + lo
+    grid = _noise_grid(H, W, cell, gen, lo, hi, device)
     ys = (torch.arange(H, dtype=torch.float64, device=device) + 0.5) / cell
     xs = (torch.arange(W, dtype=torch.float64, device=device) + 0.5) / cell
     y0, x0 = ys.floor().long(), xs.floor().long()
@@ -270,6 +283,31 @@ def grazing_plane(W=1920, H=1080, device="cpu") -> Scene:
     return Scene("grazing_plane", _f32(gbuf), None, None, mat, [Light(kind=1, dir=ldir, intensity=1.0)])
 
 
+SPHERE_PLANE = {"target": (0.0, 0.55, 0.0), "light_pos": [(2.5, 3.5, 2.0), (-3.0, 2.5, -1.5)],
+                "light_I": [12.0, 8.0]}
+
+
+def sphere_plane_setup(W=3840, H=2160, azimuth_deg=0.0, seed=3):
+    """Everything that defines the sphere_plane frame, for a generator that
+    rebuilds it elsewhere: camera (eye, fwd, right, up, tan of half the
+    vertical field of view), geometry and lights, and the two value-noise
+    lattices (alpha, log10 density) drawn from the seeded generator in the
+    same order as sphere_plane."""
+    az = math.radians(azimuth_deg)
+    R = 4.2
+    eye = (R * math.sin(az), 1.6, R * math.cos(az))
+    cam = camera_basis(eye, SPHERE_PLANE["target"])
+    gen = torch.Generator().manual_seed(seed)
+    alpha = _noise_grid(H, W, 64, gen, 0.05, 0.5, "cpu")
+    log10rho = _noise_grid(H, W, 64, gen, 3.0, 9.0, "cpu")
+    return dict(W=W, H=H, camera=cam, tan_half_fov=math.tan(math.radians(60.0) / 2), center=(0.0, 1.0, 0.0),
+                radius=1.0, sphere_uv_scale=8.0, plane_half_extent=10.0, plane_uv_scale=4.0, plane_uv_wrap=8.0,
+                light_pos=SPHERE_PLANE["light_pos"], light_I=SPHERE_PLANE["light_I"], noise_cell=64,
+                noise_alpha=alpha, noise_log10_density=log10rho,
+                material=Material(ndf=0, alpha_x=0.3, alpha_y=0.3, ln_density=math.log(1e6), n_lods=12),
+                lights=[Light(kind=0), Light(kind=0)])
+
+
 def sphere_plane(W=3840, H=2160, azimuth_deg=0.0, seed=3, device="cpu") -> Scene:
     """Unit sphere resting on a 20 x 20 ground plane.  Sphere uv is
     equirectangular x 8, plane uv is 4 x world wrapped to [0, 8).  Per-pixel
@@ -278,7 +316,7 @@ def sphere_plane(W=3840, H=2160, azimuth_deg=0.0, seed=3, device="cpu") -> Scene
     az = math.radians(azimuth_deg)
     R = 4.2
     eye = (R * math.sin(az), 1.6, R * math.cos(az))
-    eye_t, D, dDdx, dDdy = camera_rays(W, H, eye, (0.0, 0.55, 0.0), 60.0, device)
+    eye_t, D, dDdx, dDdy = camera_rays(W, H, eye, SPHERE_PLANE["target"], 60.0, device)
     center = torch.tensor([0.0, 1.0, 0.0], dtype=torch.float64, device=device)
     ts = _hit_sphere(eye_t, D, center, 1.0)
     tp = _hit_plane(eye_t, D)
@@ -296,7 +334,7 @@ def sphere_plane(W=3840, H=2160, azimuth_deg=0.0, seed=3, device="cpu") -> Scene
     P, u, v, dudx, dvdx, dudy, dvdy, N, tg = [pick(a, b) for a, b in zip(sph, pla)]
     wv = _normalize(-D)
     gbuf = _pack(u, v, dudx, dvdx, dudy, dvdy, N, tg, wv, mask)
-    light_px = _point_lights(P, mask, [(2.5, 3.5, 2.0), (-3.0, 2.5, -1.5)], [12.0, 8.0])
+    light_px = _point_lights(P, mask, SPHERE_PLANE["light_pos"], SPHERE_PLANE["light_I"])
     gen = torch.Generator().manual_seed(seed)
     alpha = _value_noise(H, W, 64, gen, 0.05, 0.5, device)
     log10rho = _value_noise(H, W, 64, gen, 3.0, 9.0, device)
@@ -378,6 +416,20 @@ def _hit_heightfield(eye, D, hf, n_march=128, n_bisect=48, chunk=1 << 18):
     return t.reshape(D.shape[:-1])
 
 
+def heightmap_camera(view_deg):
+    """(eye, target, up) of the heightmap views: height 1, the central ray
+    meeting the base plane at view_deg."""
+    v = math.radians(view_deg)
+    return (0.0, 1.0, 0.0), (0.0, 1.0 - math.sin(v), -math.cos(v)), (0.0, 0.0, -1.0)
+
+
+def heightmap_material(alpha=1.0, density=1e7):
+    return Material(ndf=0, alpha_x=alpha, alpha_y=alpha, ln_density=math.log(density), n_lods=16)
+
+
+HEIGHTMAP_LIGHT_DIR = (0.0, math.sin(math.radians(30.0)), -math.cos(math.radians(30.0)))
+
+
 def heightmap(W=1920, H=1080, view_deg=25.0, seed=5, alpha=1.0, density=1e7, rms_slope=0.45,
               device="cpu") -> Scene:
     """Plane y = 0 displaced by a high-frequency seeded heightfield (16
@@ -393,10 +445,8 @@ def heightmap(W=1920, H=1080, view_deg=25.0, seed=5, alpha=1.0, density=1e7, rms
     density sweep to 1e10 stays on the pyramid), one directional light at
     30 degrees elevation.  rms_slope = 0 gives the flat plane of the same
     views (the Plane 90 / 25 degree scenes of Table 1)."""
-    v = math.radians(view_deg)
-    eye = (0.0, 1.0, 0.0)
-    target = (0.0, 1.0 - math.sin(v), -math.cos(v))
-    eye_t, D, dDdx, dDdy = camera_rays(W, H, eye, target, 30.0, device, up=(0.0, 0.0, -1.0))
+    eye, target, up = heightmap_camera(view_deg)
+    eye_t, D, dDdx, dDdy = camera_rays(W, H, eye, target, 30.0, device, up=up)
     if not bool((D[..., 1] < 0).all()):
         raise ValueError("heightmap: every ray must point below the horizon (view_deg > 15)")
     hf = Heightfield.seeded(seed, rms_slope=rms_slope).to(device)
@@ -415,12 +465,10 @@ def heightmap(W=1920, H=1080, view_deg=25.0, seed=5, alpha=1.0, density=1e7, rms
     wv = _normalize(-D)
     mask = torch.ones_like(t, dtype=torch.bool)
     gbuf = _pack(u, v_, dudx, dvdx, dudy, dvdy, N, tg, wv, mask)
-    el = math.radians(30.0)
-    ldir = (0.0, math.sin(el), -math.cos(el))
-    mat = Material(ndf=0, alpha_x=alpha, alpha_y=alpha, ln_density=math.log(density), n_lods=16)
+    mat = heightmap_material(alpha, density)
     name = "heightmap" if rms_slope > 0 else "plane"
     return Scene(f"{name}{int(round(view_deg))}", _f32(gbuf), None, None, mat,
-                 [Light(kind=1, dir=ldir, intensity=1.0)])
+                 [Light(kind=1, dir=HEIGHTMAP_LIGHT_DIR, intensity=1.0)])
 
 
 ORBIT_RESOLUTIONS = [(256, 256), (512, 512), (1280, 720), (1920, 1080)]
