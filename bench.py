@@ -493,7 +493,7 @@ def run_heightmap(args, dev):
     for surface, slope in (("plane", 0.0), ("heightmap", 0.45)):
         res[surface] = {}
         for view in (90.0, 25.0):
-            sc = scenes.heightmap(view_deg=view, rms_slope=slope, device=dev)
+            sc = glint.gbuffer_heightmap(view_deg=view, rms_slope=slope, device=dev)    # GPU ray march
             out = torch.empty(sc.height, sc.width, dtype=torch.float32, device=dev)
             g = sc.gbuf.reshape(-1, 16).double()
             J = torch.stack([torch.stack([g[:, 2], g[:, 4]], -1), torch.stack([g[:, 3], g[:, 5]], -1)], -2)

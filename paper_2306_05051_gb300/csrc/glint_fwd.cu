@@ -169,7 +169,7 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
 #pragma unroll 1
             for (int ii = 0; ii < (kIso ? 2 : 4); ++ii) {
                 const int i = kIso ? 3 * ii : ii;
-                const float shade_i = L.shade * S.wmix[i];        // wmix = 1 unless lod_blend = 1
+                const float shade_i = P.lod_blend ? L.shade * S.wmix[i] : L.shade;   // linear-mix ablation
                 if (kClassical) {
                     if (!vertex_used(P.M, i) || !L.on) continue;
                     const ClassicalLaw cl = classical_law(S.ntr[i], S.ntr_lo[i], L.p, L.p_lo);

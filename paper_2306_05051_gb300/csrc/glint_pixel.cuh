@@ -629,17 +629,29 @@ static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T,
         us = us + (oa * S.u0x - ob * S.u0y);
         vs = vs + (oa * S.u0y + ob * S.u0x);
     }
+    // Tetrahedron vertices 0 and 3 are the same ratio / orientation grid at
+    // levels l and l + 1 (prism split, setup_pixel): with f = 4 the level
+    // factor halves exactly, so vertex 3's lattice coordinate is vertex 0's
+    // scaled by 1/2, bit for bit.
+    df qx0, qy0;
 #pragma unroll 1
     for (int ii = 0; ii < (kIso ? 2 : 4); ++ii) {
         const int i = kIso ? 3 * ii : ii;
         const Vert V = S.vert[i];
         U.gid[i] = ((uint32_t)V.level << 16) | ((uint32_t)V.ring << 8) | (uint32_t)V.kor;
-        const RotEntry Q = T.rot[rot_index(V.ring, V.kor)];
-        df sl;
-        if (P.f == 4) sl = scale2(S.srho, -V.level);
-        else sl = (V.level & 1) ? scale2(S.srho * ldf(T.d.inv_sqrt2), -(V.level >> 1)) : scale2(S.srho, -(V.level >> 1));
-        const df qx = sl * (df{Q.r0.x, Q.r0.y} * us + df{Q.r0.z, Q.r0.w} * vs);
-        const df qy = sl * (df{Q.r1.x, Q.r1.y} * us + df{Q.r1.z, Q.r1.w} * vs);
+        df qx, qy;
+        if (i == 3 && P.f == 4) {
+            qx = scale2(qx0, -1);
+            qy = scale2(qy0, -1);
+        } else {
+            const RotEntry Q = T.rot[rot_index(V.ring, V.kor)];
+            df sl;
+            if (P.f == 4) sl = scale2(S.srho, -V.level);
+            else sl = (V.level & 1) ? scale2(S.srho * ldf(T.d.inv_sqrt2), -(V.level >> 1)) : scale2(S.srho, -(V.level >> 1));
+            qx = sl * (df{Q.r0.x, Q.r0.y} * us + df{Q.r0.z, Q.r0.w} * vs);
+            qy = sl * (df{Q.r1.x, Q.r1.y} * us + df{Q.r1.z, Q.r1.w} * vs);
+            if (i == 0) { qx0 = qx; qy0 = qy; }
+        }
         if (!(fabsf(qx.hi) < 1073741824.0f) || !(fabsf(qy.hi) < 1073741824.0f)) return false;
         df fxd, fyd;
         const int i0 = dffloor(qx, &fxd);
