@@ -34,10 +34,13 @@ METRIC = "glint-shaded Gpixel/s at 4K (fwd, batched vs plain) + fwd+bwd ms; % of
 WORKLOAD = "sphere_plane 3840x2160, 2 point lights, per-pixel alpha U[0.05,0.5] and log10 density U[3,9], 12 LODs"
 
 # Algorithmic work per unit, from the hot-path scope table: about 3-3.5 k
-# issued lane instructions per shaded pixel and light (48 evaluations of ~40
-# hash + ~20 quantile + ~8 gate/floor/accumulate operations, plus ~400 of
-# setup); the midpoint is the roofline's unit.
-OPS_PER_PIXEL_LIGHT_SCOPE = 3250
+# issued lane instructions per shaded pixel and light, made of ~60 per
+# binomial evaluation (hash ~30-40, quantile ~15-25, gate / floor /
+# accumulate ~8) times 48 evaluations, plus ~400 of per-pixel setup.  A
+# launch's work is counted from its exact census: 60 per evaluation (48 per
+# sub-footprint and light, 24 with isotropic grids) plus 400 per pixel-light.
+OPS_PER_EVAL_SCOPE = 60
+OPS_PER_PIXEL_LIGHT_SCOPE = 400
 # A lower bound kept beside it: the minimal FP32 / INT32 operations of each
 # step of the method as specified (see the design notes):
 OPS_PER_PIXEL = 120        # frame, footprint SVD / atan2 / log2, split
@@ -289,13 +292,15 @@ def peak_lane_ops():
 
 def roofline_of(cen, ms, factor=1.0):
     """ALU roofline of `factor` x the work of census `cen` in ms: the scope
-    table's 3250 lane-ops per pixel-light, and the minimal-op count beside it."""
+    table's 60 lane-ops per evaluation and 400 per pixel-light, and the
+    minimal-op count beside it."""
     peak = peak_lane_ops()
-    ops = OPS_PER_PIXEL_LIGHT_SCOPE * cen["pl"] * factor
+    ops = (OPS_PER_EVAL_SCOPE * cen["evals"] + OPS_PER_PIXEL_LIGHT_SCOPE * cen["pl"]) * factor
     a = ops / (ms * 1e-3) / 1e12
     a_min = cen["ops"] * factor / (ms * 1e-3) / 1e12
     return {"bound": "alu", "achieved": a, "peak": peak, "unit": "T lane-op/s", "frac": a / peak,
-            "algorithmic_ops": ops, "ops_per_pixel_light": OPS_PER_PIXEL_LIGHT_SCOPE,
+            "algorithmic_ops": ops, "ops_per_evaluation": OPS_PER_EVAL_SCOPE,
+            "ops_per_pixel_light": OPS_PER_PIXEL_LIGHT_SCOPE,
             "frac_minimal_ops": a_min / peak, "minimal_ops": cen["ops"] * factor}
 
 
@@ -454,15 +459,17 @@ def run_ablations(args, dev):
     """The schemes the paper replaces, as material modes of the same kernel,
     on the 1080p grazing plane (C2) over a sweep of flake densities: the
     classical Gaussian / Bernoulli-loop sampler (Sec. 6.3; its cost depends
-    on N and p, Sec. 7.1) against the gated sampler, and the linear mix of
-    LOD outputs (Sec. 3) against the distributed binomial."""
+    on N and p, Sec. 7.1) against the gated sampler, the linear mix of LOD
+    outputs (Sec. 3) against the distributed binomial, and the uniforms read
+    from the precomputed random-number table (Sec. 6.3) against the hash."""
     import dataclasses
     from paper_2306_05051_gb300 import glint, scenes
     sc = scenes.grazing_plane(device=dev)
     out = torch.empty(sc.height, sc.width, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
     res = {"workload": "grazing_plane 1920x1080, directional light, anisotropy to 32:1 (C2), 12 LODs"}
-    for name, kw in (("gated", {}), ("classical", {"sampler": 1}), ("linear_mix", {"lod_blend": 1})):
+    for name, kw in (("gated", {}), ("classical", {"sampler": 1}), ("linear_mix", {"lod_blend": 1}),
+                     ("rng_table", {"rng_table": 1})):
         per = {}
         for rho in (1e3, 1e4, 1e5, 1e6, 1e7):
             m = dataclasses.replace(sc.material, ln_density=math.log(rho), **kw)
@@ -471,8 +478,9 @@ def run_ablations(args, dev):
         per["ms_min_max"] = [min(ms), max(ms)]
         per["max_over_min"] = max(ms) / min(ms)
         res[name] = per
-    res["classical_over_gated_time"] = {k: res["classical"][k] / res["gated"][k] for k in res["gated"]
-                                        if k.startswith("density_")}
+    for name in ("classical", "linear_mix", "rng_table"):
+        res[f"{name}_over_gated_time"] = {k: res[name][k] / res["gated"][k] for k in res["gated"]
+                                          if k.startswith("density_")}
     return res
 
 
