@@ -171,7 +171,7 @@ def census(glint, scene_dev, material=None):
     material = material or scene_dev.material
     per = 24 if material.n_rings == 0 else 48          # evaluations per sub-footprint and light
     n = scene_dev.width * scene_dev.height
-    tot = dict(px=0, sub=0, pl=0, sl=0, evals=0)
+    tot = dict(px=0, sub=0, pl=0, sl=0, evals=0, evals_can_open=0)
     chunk = 1 << 21
     for s in range(0, n, chunk):
         pix, _ = glint.trace(scene_dev, np.arange(s, min(n, s + chunk), dtype=np.int32), cap=0, material=material)
@@ -181,6 +181,7 @@ def census(glint, scene_dev, material=None):
         lights_on = np.where(K > 0, nrec // (per * np.maximum(K, 1)), 0)
         tot["px"] += int(ok.sum()); tot["sub"] += int(K.sum()); tot["pl"] += int(lights_on.sum())
         tot["sl"] += int((K * lights_on).sum()); tot["evals"] += int(nrec.sum())
+        tot["evals_can_open"] += int(pix["n_can_open"][ok].astype(np.int64).sum())
     # isotropic-grid mode: 2 grid vertices instead of 4 (2 grid transforms and
     # 6 spatial hashes per sub-footprint, 2 count laws per sub-footprint-light)
     o_sub, o_sl = (OPS_PER_SUB, OPS_PER_SUB_LIGHT) if per == 48 else (OPS_PER_SUB_ISO, OPS_PER_SUB_LIGHT // 2)
@@ -298,7 +299,12 @@ def roofline_of(cen, ms, factor=1.0):
     ops = (OPS_PER_EVAL_SCOPE * cen["evals"] + OPS_PER_PIXEL_LIGHT_SCOPE * cen["pl"]) * factor
     a = ops / (ms * 1e-3) / 1e12
     a_min = cen["ops"] * factor / (ms * 1e-3) / 1e12
+    # the kernels skip grid vertices and lights whose gates cannot open
+    # (their evaluations add exactly 0): the work of the evaluations that can
+    a_req = (OPS_PER_EVAL_SCOPE * cen["evals_can_open"] + OPS_PER_PIXEL_LIGHT_SCOPE * cen["pl"]) * factor \
+        / (ms * 1e-3) / 1e12
     return {"bound": "alu", "achieved": a, "peak": peak, "unit": "T lane-op/s", "frac": a / peak,
+            "frac_evals_that_can_open": a_req / peak, "evals_can_open": cen["evals_can_open"] * factor,
             "algorithmic_ops": ops, "ops_per_evaluation": OPS_PER_EVAL_SCOPE,
             "ops_per_pixel_light": OPS_PER_PIXEL_LIGHT_SCOPE,
             "frac_minimal_ops": a_min / peak, "minimal_ops": cen["ops"] * factor}

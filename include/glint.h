@@ -363,7 +363,8 @@ typedef struct GlintTracePix {
     int32_t status;          /* 0 shaded, 1 background, 2 invalid, 3 lattice out of range */
     int32_t K;               /* sub-footprints */
     int32_t n_rec;           /* evaluation records produced (lights facing away produce none) */
-    int32_t pad;
+    int32_t n_can_open;      /* of those, the records whose gate can open (P>=1 > 2^-26); the image
+                                kernels skip a grid vertex, and a light, whose gates cannot */
     float   A, r, phi, out;  /* flakes in footprint, ratio, orientation, radiance */
 } GlintTracePix;
 

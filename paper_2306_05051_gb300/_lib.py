@@ -67,7 +67,7 @@ class GlintFrame(C.Structure):
                 ("width", C.c_int32), ("height", C.c_int32), ("n_lights", C.c_int32)]
 
 
-TRACE_PIX_DTYPE = np.dtype([("status", "i4"), ("K", "i4"), ("n_rec", "i4"), ("pad", "i4"),
+TRACE_PIX_DTYPE = np.dtype([("status", "i4"), ("K", "i4"), ("n_rec", "i4"), ("n_can_open", "i4"),
                             ("A", "f4"), ("r", "f4"), ("phi", "f4"), ("out", "f4")])
 TRACE_REC_DTYPE = np.dtype([("light", "i4"), ("sub", "i4"), ("vert", "i4"), ("sv", "i4"), ("av", "i4"),
                             ("gid", "u4"), ("i", "i4"), ("j", "i4"), ("ax", "i4"), ("ay", "i4"),

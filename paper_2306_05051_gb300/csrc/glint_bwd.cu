@@ -152,10 +152,15 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
     if (S.status != 0) return 0.0f;
     float out = 0.0f, outd = 0.0f;
     float gm[3] = {0.0f, 0.0f, 0.0f};         // alpha_x, alpha_y, ln density
+    // the largest trial count of the tetrahedron (P>=1 grows with N)
+    const float n_max = fmaxf(fmaxf(S.ntr[0], S.ntr[1]), fmaxf(S.ntr[2], S.ntr[3]));
     for (int l = 0; l < F.nL; ++l) {
         LightState L;
         setup_light<false>(P, T, F, S, px, l, L);       // no angular texel record needed
         if (!L.on) continue;
+        // no gate can open (P>=1 <= 2^-26 at the largest count): the light adds
+        // nothing to the relaxed image or to any derivative
+        if (L.p < 1.0f && -expm1f(n_max * L.lq) <= 1.4901161193847656e-8f) continue;
         LightGrad LG;
         light_grad(P, F, S, px, l, L, LG);
         float C = 0.0f, Cd = 0.0f, Su = 0.0f, Svx = 0.0f, Svy = 0.0f;
@@ -176,6 +181,7 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
             for (int i = 0; i < 4; ++i) {
                 if (!vertex_used(P.M, i)) continue;
                 const CountLaw law = count_law(S.ntr[i], S.ntr_lo[i], L.p, L.p_lo, L.lq);
+                if (law.Tg <= 1u) continue;              // no gate of this grid can open
                 // the 12 gates of this grid vertex first, then the open ones in
                 // (simplex vertex, texel) order
                 unsigned om = 0u;

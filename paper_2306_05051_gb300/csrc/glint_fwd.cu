@@ -133,12 +133,19 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
     if (valid) setup_pixel<false>(P, T, F, px, S);
     LightState ls[kMaxLights];
     bool any_on = false;
+    // the largest trial count of the tetrahedron: P>=1 grows with N, so a
+    // light whose gates cannot open at this count (P>=1 <= 2^-26, half of the
+    // gate's resolution) opens none at any vertex and adds nothing
+    const float n_max = fmaxf(fmaxf(S.ntr[0], S.ntr[1]), fmaxf(S.ntr[2], S.ntr[3]));
     for (int l = 0; l < F.nL; ++l) {
         ls[l].on = false;
         if (S.status == 0) setup_light<false>(P, T, F, S, px, l, ls[l]);
+        if (ls[l].on && ls[l].p < 1.0f && !kClassical && -expm1f(n_max * ls[l].lq) <= 1.4901161193847656e-8f)
+            ls[l].on = false;
         any_on |= ls[l].on;
     }
-    // a pixel that no light reaches shades to 0: its sub-footprints are not set up
+    // a pixel that no light reaches, or whose gates cannot open, shades to 0:
+    // its sub-footprints are not set up
     const int K = S.status == 0 && any_on ? S.K : 0;
     const int Kw = __reduce_max_sync(0xffffffffu, K);
     float acc = 0.0f;
@@ -187,6 +194,10 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
                 }
                 CountLaw law = count_law(S.ntr[i], S.ntr_lo[i], L.p, L.p_lo, L.lq);
                 if (!L.on) law.Tg = 0u;
+                // no gate of this grid can open in any lane (P>=1 below 2^-25,
+                // e.g. a half-vector far from the NDF's peak): its 12
+                // evaluations add nothing
+                if (!__any_sync(0xffffffffu, law.Tg > 1u)) continue;
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     const uint32_t s0 = s0s[(3 * i + j) * st], s1 = U.S1[3 * i + j];
@@ -317,7 +328,7 @@ __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& 
                             GlintTraceRec* recs, int cap) {
     PixelSetup S;
     setup_pixel<true>(P, T, F, px, S);
-    pr->status = S.status; pr->K = S.status == 0 ? S.K : 0; pr->n_rec = 0; pr->pad = 0;
+    pr->status = S.status; pr->K = S.status == 0 ? S.K : 0; pr->n_rec = 0; pr->n_can_open = 0;
     pr->A = S.status == 0 ? S.A.hi : 0.0f; pr->r = S.status == 0 ? S.ratio.hi : 0.0f;
     pr->phi = S.status == 0 ? S.phi.hi : 0.0f; pr->out = 0.0f;
     if (S.status != 0) return;
@@ -325,12 +336,12 @@ __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& 
     for (int l = 0; l < F.nL; ++l) setup_light<true>(P, T, F, S, px, l, ls[l]);
     float C[kMaxLights];
     for (int l = 0; l < F.nL; ++l) C[l] = 0.0f;
-    int nrec = 0;
+    int nrec = 0, ncan = 0;
     for (int sub = 0; sub < S.K; ++sub) {
         SubState U;
         const bool ok = P.M > 0 ? setup_sub<true, false>(P, T, S, sub, U, U.S0, U.uw, 1)
                                 : setup_sub<true, true>(P, T, S, sub, U, U.S0, U.uw, 1);
-        if (!ok) { pr->status = 3; pr->n_rec = nrec; return; }
+        if (!ok) { pr->status = 3; pr->n_rec = nrec; pr->n_can_open = ncan; return; }
         for (int l = 0; l < F.nL; ++l) {
             const LightState& L = ls[l];
             if (!L.on) continue;
@@ -360,6 +371,7 @@ __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& 
                         if (g) C[l] += U.uw[3 * i + j] * L.v[k] * (S.wmix[i] * c);
                         const int idx = (((l * S.K + sub) * 4 + i) * 3 + j) * 4 + k;
                         ++nrec;
+                        ncan += (P.sampler || law.Tg > 1u) ? 1 : 0;
                         if (idx < cap) {
                             GlintTraceRec& R = recs[idx];
                             R.light = l; R.sub = sub; R.vert = i; R.sv = j; R.av = k; R.grid_id = U.gid[i];
@@ -380,6 +392,7 @@ __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& 
         if (ls[l].on) out += ls[l].shade * C[l];
     pr->out = out / S.A.hi;
     pr->n_rec = nrec;
+    pr->n_can_open = ncan;
 }
 
 __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ KParams P, const FrameDesc F,
@@ -391,7 +404,7 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ KPar
     if (k >= n_px) return;
     const int px = px_list[k];
     if (px < 0 || px >= F.npx) {
-        pix[k].status = 2; pix[k].K = 0; pix[k].n_rec = 0; pix[k].pad = 0;
+        pix[k].status = 2; pix[k].K = 0; pix[k].n_rec = 0; pix[k].n_can_open = 0;
         pix[k].A = pix[k].r = pix[k].phi = pix[k].out = 0.0f;
         return;
     }
