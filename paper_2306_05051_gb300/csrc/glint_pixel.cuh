@@ -262,17 +262,21 @@ struct Vert {           // one tetrahedron vertex (a virtual grid)
 // --------------------------------------------------------------------------
 // Steps 1-5: everything about a pixel that does not depend on a light
 // --------------------------------------------------------------------------
+// The struct lives on the per-thread stack (setup_sub takes it by reference),
+// so each stored field costs stack traffic: what the image kernels do not
+// read again is stored for the trace and adjoint kernels only.
 struct PixelSetup {
     int status;         // 0 shaded, 1 background, 2 invalid
     int K, Kmaj, ksub;
     df A;               // flakes in the footprint
-    df ratio, phi;
-    df u, v;            // centre uv (exact float inputs)
+    df ratio, phi;      // (traces only)
+    float u, v;         // centre uv (exact float inputs)
     df sig0, sig1, u0x, u0y;
-    Vert vert[4];
+    uint32_t vgid[4];   // tetrahedron vertices as grid ids: level << 16 | ring << 8 | orientation
     float ntr[4];       // trials of the 4 tetrahedron vertices (per sub-footprint)
     float ntr_lo[4];    // their low words (double-float trials)
-    float wmix[4];      // linear mix (lod_blend = 1): LOD weight of each vertex's count; else 1
+    float wmix[4];      // linear mix (lod_blend = 1): LOD weight of each vertex's count; else 1 (set
+                        // for traces only: the image kernels read it only with lod_blend)
     float dntr[4];      // d ntr / d ln(density) (adjoint)
     df srho;
     // shading frame and view direction (local frame), for the lights
@@ -365,15 +369,16 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
     const df hyp = dfsqrt(hm * hm + jF * jF);
     const df s0sq = scale2(jE + jG, -1) + hyp;
     // ratio sigma0 / max(sigma1, 2^-20 sigma0): finite for line-like footprints
-    S.ratio = dflt(s0sq, scale2(det, 20)) ? s0sq / det : mkdf(1048576.0f);
-    S.phi = scale2(dfatan2(scale2(jF, 1), jE - jG, T.d), -1);
-    if (dfsign(S.phi) < 0) S.phi = S.phi + ldf(T.d.pi);
-    if (!dflt(S.phi, ldf(T.d.pi))) S.phi = S.phi - ldf(T.d.pi);
-    S.u = mkdf(g0.x); S.v = mkdf(g0.y);
+    const df ratio = dflt(s0sq, scale2(det, 20)) ? s0sq / det : mkdf(1048576.0f);
+    df phi = scale2(dfatan2(scale2(jF, 1), jE - jG, T.d), -1);
+    if (dfsign(phi) < 0) phi = phi + ldf(T.d.pi);
+    if (!dflt(phi, ldf(T.d.pi))) phi = phi - ldf(T.d.pi);
+    if (kTrace) { S.ratio = ratio; S.phi = phi; }
+    S.u = g0.x; S.v = g0.y;
 
     // ---- 3. sub-footprints --------------------------------------------
     int Kmaj = 1;
-    const df rq = scale2(S.ratio, -P.M);
+    const df rq = scale2(ratio, -P.M);
     if (dfsign(rq - 1.0f) > 0) {
         df fr;
         int c = dffloor(rq, &fr);           // rq <= 2^19 (ratio capped at 2^20)
@@ -388,7 +393,7 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
     const int K = Kmaj * ksub * ksub;
     S.Kmaj = Kmaj; S.ksub = ksub; S.K = K;
     const df As = K == 1 ? S.A : A_over(S.A, K);
-    const df lr = dflog2(S.ratio, T.d);
+    const df lr = dflog2(ratio, T.d);
     const df rho_r = Kmaj == 1 ? lr : lr - dflog2(mkdf((float)Kmaj), T.d);
     if (K > 1) {
         // major axis u0 of the footprint (eigenvector of J J^T for sigma0^2),
@@ -428,7 +433,7 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
     const df x = rr - (float)m;
     const int nm = m == 0 ? 4 : (1 << (m + 1));
     df t;
-    int a = dffloor(scale2(S.phi * ldf(T.d.inv_pi), m == 0 ? 2 : m + 1), &t);
+    int a = dffloor(scale2(phi * ldf(T.d.inv_pi), m == 0 ? 2 : m + 1), &t);
     a %= nm;
     // triangle vertices (ring, orientation) and barycentrics; scalars, not
     // arrays, so nothing below is indexed at run time
@@ -474,26 +479,27 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int k = (c + i) % 3;
-        S.vert[i].ring = k == 0 ? r0 : (k == 1 ? r1 : r2);
-        S.vert[i].kor = k == 0 ? k0 : (k == 1 ? k1 : k2);
-        S.vert[i].level = level + (i >= 3 - c ? 1 : 0);
-        const df ni = pinned ? w[i] * As : scale2(w[i], S.vert[i].level * P.log2f);
+        const int vring = k == 0 ? r0 : (k == 1 ? r1 : r2);
+        const int vkor = k == 0 ? k0 : (k == 1 ? k1 : k2);
+        const int vlevel = level + (i >= 3 - c ? 1 : 0);
+        S.vgid[i] = ((uint32_t)vlevel << 16) | ((uint32_t)vring << 8) | (uint32_t)vkor;
+        const df ni = pinned ? w[i] * As : scale2(w[i], vlevel * P.log2f);
         if (P.lod_blend) {
             // linear mix of LOD outputs (Sec. 3): each vertex counts over its
             // whole cell (f^level flakes; pinned: A_s) and its count is
             // weighted by w_i afterwards
-            const df nf = pinned ? As : mkdf(pow2f(S.vert[i].level * P.log2f));
+            const df nf = pinned ? As : mkdf(pow2f(vlevel * P.log2f));
             S.ntr[i] = nf.hi;
             S.ntr_lo[i] = nf.lo;
             S.wmix[i] = __fadd_rn(w[i].hi, w[i].lo);
         } else {
             S.ntr[i] = ni.hi;
             S.ntr_lo[i] = ni.lo;
-            S.wmix[i] = 1.0f;
+            if (kTrace) S.wmix[i] = 1.0f;
         }
         if (kTrace) {
             const float dw = i == 0 ? -ds : (i == 3 ? ds : 0.0f);
-            S.dntr[i] = pinned ? ni.hi : dw * pow2f((S.vert[i].level) * P.log2f);
+            S.dntr[i] = pinned ? ni.hi : dw * pow2f(vlevel * P.log2f);
         }
     }
     S.status = 0;
@@ -618,7 +624,7 @@ struct SubState {
 template <bool kTrace, bool kIso>
 static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T, const PixelSetup& S, int sub,
                                               SubState& U, uint32_t* s0, float* uwo, int stride) {
-    df us = S.u, vs = S.v;
+    df us = mkdf(S.u), vs = mkdf(S.v);
     if (S.K > 1) {
         // centre of sub-rectangle (ia, ib) of the sigma0 x sigma1 rectangle
         // aligned with (u0, u1 = (-u0y, u0x))
@@ -637,8 +643,9 @@ static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T,
 #pragma unroll 1
     for (int ii = 0; ii < (kIso ? 2 : 4); ++ii) {
         const int i = kIso ? 3 * ii : ii;
-        const Vert V = S.vert[i];
-        U.gid[i] = ((uint32_t)V.level << 16) | ((uint32_t)V.ring << 8) | (uint32_t)V.kor;
+        const uint32_t gid = S.vgid[i];
+        if (kTrace) U.gid[i] = gid;
+        const Vert V = {(int)((gid >> 8) & 255u), (int)(gid & 255u), (int)(gid >> 16)};
         df qx, qy;
         if (i == 3 && P.f == 4) {
             qx = scale2(qx0, -1);
@@ -669,7 +676,7 @@ static __device__ __noinline__ bool setup_sub(const KParams& P, const Tables& T,
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             if (kTrace) { U.li[3 * i + j] = li3[j]; U.lj[3 * i + j] = lj3[j]; }
-            uint32_t hx = (uint32_t)li3[j], hy = (uint32_t)lj3[j], hz = U.gid[i], hw = P.seed;
+            uint32_t hx = (uint32_t)li3[j], hy = (uint32_t)lj3[j], hz = gid, hw = P.seed;
             pcg4d(hx, hy, hz, hw);
             s0[(3 * i + j) * stride] = hx;
             uwo[(3 * i + j) * stride] = w3[j];
