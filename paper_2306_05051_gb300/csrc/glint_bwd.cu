@@ -54,7 +54,7 @@ __device__ __forceinline__ float lambda_grad(int ndf, float ax, float ay, const 
     return lam;
 }
 
-__device__ void light_grad(const KParams& P, const FrameDesc& F, const PixelSetup& S, int px, int l,
+__device__ void light_grad(const KParams& P, const FrameDesc& F, const PixelSetup& S, const LocalFrame& R, int px, int l,
                            const LightState& L, LightGrad& G) {
     const KLight kl = P.lights[l];
     G.dir = kl.kind == 1;
@@ -68,9 +68,9 @@ __device__ void light_grad(const KParams& P, const FrameDesc& F, const PixelSetu
     const float dl = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     const float w[3] = {d[0] / dl, d[1] / dl, d[2] / dl};
     float Fr[3][3];
-    for (int c = 0; c < 3; ++c) { Fr[0][c] = S.tg[c].hi; Fr[1][c] = S.b[c].hi; Fr[2][c] = S.n[c].hi; }
+    for (int c = 0; c < 3; ++c) { Fr[0][c] = R[kFrT + 2 * c]; Fr[1][c] = R[kFrB + 2 * c]; Fr[2][c] = R[kFrN + 2 * c]; }
     float ll[3], v[3];
-    for (int r = 0; r < 3; ++r) { ll[r] = Fr[r][0] * w[0] + Fr[r][1] * w[1] + Fr[r][2] * w[2]; v[r] = S.wv[r].hi; }
+    for (int r = 0; r < 3; ++r) { ll[r] = Fr[r][0] * w[0] + Fr[r][1] * w[1] + Fr[r][2] * w[2]; v[r] = R[kFrV + 2 * r]; }
     float hs[3] = {v[0] + ll[0], v[1] + ll[1], v[2] + ll[2]};
     const float hl = sqrtf(hs[0] * hs[0] + hs[1] * hs[1] + hs[2] * hs[2]);
     const float h[3] = {hs[0] / hl, hs[1] / hl, hs[2] / hl};
@@ -82,7 +82,7 @@ __device__ void light_grad(const KParams& P, const FrameDesc& F, const PixelSetu
         const float hj = h[0] * Jl[0][c] + h[1] * Jl[1][c] + h[2] * Jl[2][c];
         for (int r = 0; r < 3; ++r) Jh[r][c] = (Jl[r][c] - h[r] * hj) / hl;
     }
-    const float ax = S.ax, ay = S.ay, ht = h[0], hb = h[1], hn = h[2];
+    const float ax = R[kFrAx], ay = R[kFrAy], ht = h[0], hb = h[1], hn = h[2];
     // Eq. 4: p = R D(h)/D(n)
     const float e = (ht / ax) * (ht / ax) + (hb / ay) * (hb / ay);
     float dr_dh[3], dr_da[2];
@@ -126,11 +126,11 @@ __device__ void light_grad(const KParams& P, const FrameDesc& F, const PixelSetu
     const float Dn = 1.0f / (3.14159265358979f * ax * ay);
     float E;
     if (kl.kind == 0) E = __ldg(F.light_px + (size_t)l * F.lstride + px).w; else E = kl.E;
-    const float base = Dn * E / (4.0f * P.R * S.cos_v);
+    const float base = Dn * E / (4.0f * P.R * R[kFrCosV]);
     for (int c = 0; c < 2; ++c) {
         const float dG = -Gs * (dlv_da[c] / (1.0f + lam_v) + dll_da[c] / (1.0f + lam_l));
         const float dDn = -Dn / (c == 0 ? ax : ay);
-        G.ds_da[c] = Fr_ * (dG * Dn + Gs * dDn) * E / (4.0f * P.R * S.cos_v);
+        G.ds_da[c] = Fr_ * (dG * Dn + Gs * dDn) * E / (4.0f * P.R * R[kFrCosV]);
     }
     for (int c = 0; c < 3; ++c) {
         const float dvh = v[0] * Jh[0][c] + v[1] * Jh[1][c] + v[2] * Jh[2][c];
@@ -148,7 +148,8 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
     for (int k = 0; k < ng; ++k) g[k] = 0.0f;
     *disc = 0.0f;
     PixelSetup S;
-    setup_pixel<true>(P, T, F, px, S);
+    LocalFrame R;
+    setup_pixel<true>(P, T, F, px, S, R);
     if (S.status != 0) return 0.0f;
     float out = 0.0f, outd = 0.0f;
     float gm[3] = {0.0f, 0.0f, 0.0f};         // alpha_x, alpha_y, ln density
@@ -156,13 +157,13 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
     const float n_max = fmaxf(fmaxf(S.ntr[0], S.ntr[1]), fmaxf(S.ntr[2], S.ntr[3]));
     for (int l = 0; l < F.nL; ++l) {
         LightState L;
-        setup_light<false>(P, T, F, S, px, l, L);       // no angular texel record needed
+        setup_light<false>(P, T, F, S, R, px, l, L);       // no angular texel record needed
         if (!L.on) continue;
         // no gate can open (P>=1 <= 2^-26 at the largest count): the light adds
         // nothing to the relaxed image or to any derivative
         if (L.p < 1.0f && -expm1f(n_max * L.lq) <= 1.4901161193847656e-8f) continue;
         LightGrad LG;
-        light_grad(P, F, S, px, l, L, LG);
+        light_grad(P, F, S, R, px, l, L, LG);
         float C = 0.0f, Cd = 0.0f, Su = 0.0f, Svx = 0.0f, Svy = 0.0f;
         float dC[3] = {0.0f, 0.0f, 0.0f}, dCd[3] = {0.0f, 0.0f, 0.0f};
         const float p = L.p;

@@ -64,6 +64,8 @@ struct WarpQueue {
     float res[32];
     uint32_t mask[32];
 };
+// (its first 16 x 32 words also hold the lanes' shading frames, SharedFrame)
+static_assert(sizeof(WarpQueue) >= 16 * 32 * sizeof(float), "warp queue too small for the frame words");
 
 // Copy the double-float tables (only the rotation entries up to ring M)
 // from the parameter block into shared memory.
@@ -130,7 +132,11 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
     PixelSetup S;
     S.status = 1;
     S.K = 0;
-    if (valid) setup_pixel<false>(P, T, F, px, S);
+    // the shading frame lives in this lane's slots of the warp's queue and
+    // spatial words until the lights are set up
+    const SharedFrame R{reinterpret_cast<float*>(&q) + lane, reinterpret_cast<float*>(ss0) + threadIdx.x,
+                        (int)blockDim.x};
+    if (valid) setup_pixel<false>(P, T, F, px, S, R);
     LightState ls[kMaxLights];
     bool any_on = false;
     // the largest trial count of the tetrahedron: P>=1 grows with N, so a
@@ -139,11 +145,12 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
     const float n_max = fmaxf(fmaxf(S.ntr[0], S.ntr[1]), fmaxf(S.ntr[2], S.ntr[3]));
     for (int l = 0; l < F.nL; ++l) {
         ls[l].on = false;
-        if (S.status == 0) setup_light<false>(P, T, F, S, px, l, ls[l]);
+        if (S.status == 0) setup_light<false>(P, T, F, S, R, px, l, ls[l]);
         if (ls[l].on && ls[l].p < 1.0f && !kClassical && -expm1f(n_max * ls[l].lq) <= 1.4901161193847656e-8f)
             ls[l].on = false;
         any_on |= ls[l].on;
     }
+    __syncwarp();   // the frame's slots go back to the queue and the spatial words
     // a pixel that no light reaches, or whose gates cannot open, shades to 0:
     // its sub-footprints are not set up
     const int K = S.status == 0 && any_on ? S.K : 0;
@@ -327,13 +334,14 @@ size_t fwd_smem_bytes(int threads) {
 __device__ void trace_pixel(const KParams& P, const Tables& T, const FrameDesc& F, int px, GlintTracePix* pr,
                             GlintTraceRec* recs, int cap) {
     PixelSetup S;
-    setup_pixel<true>(P, T, F, px, S);
+    LocalFrame R;
+    setup_pixel<true>(P, T, F, px, S, R);
     pr->status = S.status; pr->K = S.status == 0 ? S.K : 0; pr->n_rec = 0; pr->n_can_open = 0;
     pr->A = S.status == 0 ? S.A.hi : 0.0f; pr->r = S.status == 0 ? S.ratio.hi : 0.0f;
     pr->phi = S.status == 0 ? S.phi.hi : 0.0f; pr->out = 0.0f;
     if (S.status != 0) return;
     LightState ls[kMaxLights];
-    for (int l = 0; l < F.nL; ++l) setup_light<true>(P, T, F, S, px, l, ls[l]);
+    for (int l = 0; l < F.nL; ++l) setup_light<true>(P, T, F, S, R, px, l, ls[l]);
     float C[kMaxLights];
     for (int l = 0; l < F.nL; ++l) C[l] = 0.0f;
     int nrec = 0, ncan = 0;

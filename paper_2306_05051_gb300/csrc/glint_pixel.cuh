@@ -279,10 +279,38 @@ struct PixelSetup {
                         // for traces only: the image kernels read it only with lod_blend)
     float dntr[4];      // d ntr / d ln(density) (adjoint)
     df srho;
-    // shading frame and view direction (local frame), for the lights
-    df n[3], tg[3], b[3], wv[3];
-    float ax, ay, cos_v, lam_v;
 };
+
+// Shading frame (n, t, b) and view direction in it, double-float (24 words),
+// with the roughness, the view's cosine and Smith Lambda (4 words): written by
+// setup_pixel, read by setup_light and then dead.  The store decides where the
+// 28 words live: LocalFrame keeps them with the thread (trace and adjoint
+// kernels); the image kernels lend them slots of shared memory that stay idle
+// until the sub-footprints are set up (SharedFrame), which keeps them off the
+// per-thread stack.
+constexpr int kFrN = 0, kFrT = 6, kFrB = 12, kFrV = 18;    // df vectors: word 2c (hi), 2c + 1 (lo)
+constexpr int kFrAx = 24, kFrAy = 25, kFrCosV = 26, kFrLamV = 27, kFrameWords = 28;
+
+struct LocalFrame {
+    float w[kFrameWords];
+    __device__ __forceinline__ float& operator[](int k) { return w[k]; }
+    __device__ __forceinline__ float operator[](int k) const { return w[k]; }
+};
+
+// One lane's 28 words, bank-conflict free: words 0-15 in the lane's column of
+// 16 x 32 words (row stride 32), words 16-27 in a column of 12 rows of row
+// stride st.
+struct SharedFrame {
+    float* q;
+    float* s;
+    int st;
+    __device__ __forceinline__ float& operator[](int k) const { return k < 16 ? q[k * 32] : s[(k - 16) * st]; }
+};
+
+template <class FS>
+__device__ __forceinline__ df frame_df(const FS& R, int k) { return df{R[k], R[k + 1]}; }
+template <class FS>
+__device__ __forceinline__ void frame_put(FS& R, int k, df x) { R[k] = x.hi; R[k + 1] = x.lo; }
 
 // The input planes are read once per launch: streaming (evict-first) loads
 // leave the L2 to the per-thread stack of the setup state.
@@ -298,9 +326,9 @@ __device__ __forceinline__ bool load_gbuf(const FrameDesc& F, int px, float4& g0
 
 // kTrace: also store what only the trace and adjoint kernels read (d ntr /
 // d ln density).
-template <bool kTrace>
+template <bool kTrace, class FS>
 static __device__ __forceinline__ void setup_pixel(const KParams& P, const Tables& T, const FrameDesc& F, int px,
-                                                   PixelSetup& S) {
+                                                   PixelSetup& S, FS& R) {
     S.status = 2;
     S.K = 0;
     float4 g0, g1, g2, g3;
@@ -312,41 +340,52 @@ static __device__ __forceinline__ void setup_pixel(const KParams& P, const Table
     if (nr[0] == 0.0f && nr[1] == 0.0f && nr[2] == 0.0f) { S.status = 1; return; }
     const float tr[3] = {g2.y, g2.z, g2.w};
     const float vr[3] = {g3.x, g3.y, g3.z};
+    df n[3], tg[3], b[3], wv[3];
     {
         const df inl = dfrsqrt(two_prod(nr[0], nr[0]) + two_prod(nr[1], nr[1]) + two_prod(nr[2], nr[2]));
-        S.n[0] = inl * nr[0]; S.n[1] = inl * nr[1]; S.n[2] = inl * nr[2];
+        n[0] = inl * nr[0]; n[1] = inl * nr[1]; n[2] = inl * nr[2];
     }
-    const df tn = S.n[0] * tr[0] + S.n[1] * tr[1] + S.n[2] * tr[2];
-    df tp[3] = {tr[0] - tn * S.n[0], tr[1] - tn * S.n[1], tr[2] - tn * S.n[2]};
+    const df tn = n[0] * tr[0] + n[1] * tr[1] + n[2] * tr[2];
+    df tp[3] = {tr[0] - tn * n[0], tr[1] - tn * n[1], tr[2] - tn * n[2]};
     const df tl2 = tp[0] * tp[0] + tp[1] * tp[1] + tp[2] * tp[2];
     const df vl2 = two_prod(vr[0], vr[0]) + two_prod(vr[1], vr[1]) + two_prod(vr[2], vr[2]);
     if (!(tl2.hi > 0.0f) || !(vl2.hi > 0.0f)) return;
     {
         const df itl = dfrsqrt(tl2);
-        S.tg[0] = tp[0] * itl; S.tg[1] = tp[1] * itl; S.tg[2] = tp[2] * itl;
+        tg[0] = tp[0] * itl; tg[1] = tp[1] * itl; tg[2] = tp[2] * itl;
     }
-    S.b[0] = S.n[1] * S.tg[2] - S.n[2] * S.tg[1];
-    S.b[1] = S.n[2] * S.tg[0] - S.n[0] * S.tg[2];
-    S.b[2] = S.n[0] * S.tg[1] - S.n[1] * S.tg[0];
+    b[0] = n[1] * tg[2] - n[2] * tg[1];
+    b[1] = n[2] * tg[0] - n[0] * tg[2];
+    b[2] = n[0] * tg[1] - n[1] * tg[0];
     {
         const df ivl = dfrsqrt(vl2);
-        S.wv[0] = (S.tg[0] * vr[0] + S.tg[1] * vr[1] + S.tg[2] * vr[2]) * ivl;
-        S.wv[1] = (S.b[0] * vr[0] + S.b[1] * vr[1] + S.b[2] * vr[2]) * ivl;
-        S.wv[2] = (S.n[0] * vr[0] + S.n[1] * vr[1] + S.n[2] * vr[2]) * ivl;
+        wv[0] = (tg[0] * vr[0] + tg[1] * vr[1] + tg[2] * vr[2]) * ivl;
+        wv[1] = (b[0] * vr[0] + b[1] * vr[1] + b[2] * vr[2]) * ivl;
+        wv[2] = (n[0] * vr[0] + n[1] * vr[1] + n[2] * vr[2]) * ivl;
     }
-    if (dfsign(S.wv[2]) <= 0) return;
-    S.cos_v = S.wv[2].hi;
+    if (dfsign(wv[2]) <= 0) return;
+    const float cos_v = wv[2].hi;
 
     df rho = ldf(P.rho);
     S.srho = ldf(P.sqrt_rho);
-    S.ax = P.ax; S.ay = P.ay;
+    float ax = P.ax, ay = P.ay;
     if (F.mat_px) {
         const float2 mp = __ldcs(F.mat_px + px);
-        S.ax = S.ay = mp.x;
+        ax = ay = mp.x;
         rho = mkdf(mp.y);
         S.srho = dfsqrt(rho);
     }
-    S.lam_v = smith_lambda(P.ndf, S.ax, S.ay, S.wv[0].hi, S.wv[1].hi, S.cos_v);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        frame_put(R, kFrN + 2 * c, n[c]);
+        frame_put(R, kFrT + 2 * c, tg[c]);
+        frame_put(R, kFrB + 2 * c, b[c]);
+        frame_put(R, kFrV + 2 * c, wv[c]);
+    }
+    R[kFrAx] = ax;
+    R[kFrAy] = ay;
+    R[kFrCosV] = cos_v;
+    R[kFrLamV] = smith_lambda(P.ndf, ax, ay, wv[0].hi, wv[1].hi, cos_v);
 
     // ---- 2. footprint (double-float) ----------------------------------
     // J = [[a, b], [c, d]] = [[du/dx, du/dy], [dv/dx, dv/dy]], pre-scaled by
@@ -520,9 +559,9 @@ struct LightState {
 
 // kTrace: also record the angular texels (ax, ay) for the trace and adjoint
 // kernels; the image kernels skip those stores.
-template <bool kTrace>
+template <bool kTrace, class FS>
 static __device__ __forceinline__ void setup_light(const KParams& P, const Tables& T, const FrameDesc& F,
-                                                   const PixelSetup& S, int px, int l, LightState& L) {
+                                                   const PixelSetup& S, const FS& R, int px, int l, LightState& L) {
     L.on = false;
     const KLight kl = P.lights[l];
     float lr[3], E;
@@ -532,26 +571,30 @@ static __device__ __forceinline__ void setup_light(const KParams& P, const Table
     } else {
         lr[0] = kl.dx; lr[1] = kl.dy; lr[2] = kl.dz; E = kl.E;
     }
+    const float ax = R[kFrAx], ay = R[kFrAy], cos_v = R[kFrCosV];
     const df ll2 = two_prod(lr[0], lr[0]) + two_prod(lr[1], lr[1]) + two_prod(lr[2], lr[2]);
     if (!(ll2.hi > 0.0f)) return;
     // light direction in the local frame, unit length
     df wl[3];
     {
         const df il = dfrsqrt(ll2);
-        wl[0] = (S.tg[0] * lr[0] + S.tg[1] * lr[1] + S.tg[2] * lr[2]) * il;
-        wl[1] = (S.b[0] * lr[0] + S.b[1] * lr[1] + S.b[2] * lr[2]) * il;
-        wl[2] = (S.n[0] * lr[0] + S.n[1] * lr[1] + S.n[2] * lr[2]) * il;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int base = r == 0 ? kFrT : (r == 1 ? kFrB : kFrN);     // rows t, b, n of the frame
+            wl[r] = (frame_df(R, base) * lr[0] + frame_df(R, base + 2) * lr[1] + frame_df(R, base + 4) * lr[2]) * il;
+        }
     }
     if (dfsign(wl[2]) <= 0) return;
     const float cos_l = wl[2].hi;
-    df h[3] = {S.wv[0] + wl[0], S.wv[1] + wl[1], S.wv[2] + wl[2]};
+    const df wv[3] = {frame_df(R, kFrV), frame_df(R, kFrV + 2), frame_df(R, kFrV + 4)};
+    df h[3] = {wv[0] + wl[0], wv[1] + wl[1], wv[2] + wl[2]};
     {
         const df ih = dfrsqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
         h[0] = h[0] * ih; h[1] = h[1] * ih; h[2] = h[2] * ih;
     }
     const float ht = h[0].hi, hb = h[1].hi, hn = h[2].hi;
     // Eq. 4: p = R D(h) / D(n)
-    const float e = (ht / S.ax) * (ht / S.ax) + (hb / S.ay) * (hb / S.ay);
+    const float e = (ht / ax) * (ht / ax) + (hb / ay) * (hb / ay);
     const float hn2 = hn * hn;
     const float rat = P.ndf == 0 ? expf(-e / hn2) / (hn2 * hn2) : 1.0f / ((e + hn2) * (e + hn2));
     L.p = fminf(P.R * rat, 1.0f);
@@ -561,7 +604,7 @@ static __device__ __forceinline__ void setup_light(const KParams& P, const Table
     // would move it by more than the count tolerance) p is formed again in
     // double-float from the double-float half-vector.
     if (L.p < 1.0f && S.A.hi * L.p > kDfCountMean) {
-        const df tx = div_by(h[0], S.ax, approx_rcp(S.ax)), ty = div_by(h[1], S.ay, approx_rcp(S.ay));
+        const df tx = div_by(h[0], ax, approx_rcp(ax)), ty = div_by(h[1], ay, approx_rcp(ay));
         const df ed = tx * tx + ty * ty;
         const df hn2d = h[2] * h[2];
         df rd;
@@ -593,13 +636,13 @@ static __device__ __forceinline__ void setup_light(const KParams& P, const Table
         L.A0[k] = hx; L.A1[k] = hy;
     }
     // Eq. 2 with D_P = D(n)/R C/A: out_l = F G D(n) E / (4 R cos_v) * C / A
-    const float vh = S.wv[0].hi * ht + S.wv[1].hi * hb + S.cos_v * hn;
+    const float vh = wv[0].hi * ht + wv[1].hi * hb + cos_v * hn;
     const float om = 1.0f - vh;
     const float Fr = P.F0 + (1.0f - P.F0) * (om * om) * (om * om) * om;
-    const float lam_l = smith_lambda(P.ndf, S.ax, S.ay, wl[0].hi, wl[1].hi, cos_l);
-    const float Gs = 1.0f / ((1.0f + S.lam_v) * (1.0f + lam_l));
-    const float Dn = 1.0f / (3.14159265358979f * S.ax * S.ay);
-    L.shade = Fr * Gs * Dn * E / (4.0f * P.R * S.cos_v);
+    const float lam_l = smith_lambda(P.ndf, ax, ay, wl[0].hi, wl[1].hi, cos_l);
+    const float Gs = 1.0f / ((1.0f + R[kFrLamV]) * (1.0f + lam_l));
+    const float Dn = 1.0f / (3.14159265358979f * ax * ay);
+    L.shade = Fr * Gs * Dn * E / (4.0f * P.R * cos_v);
     L.on = true;
 }
 
