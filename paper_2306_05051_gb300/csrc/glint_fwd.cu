@@ -68,7 +68,11 @@ struct WarpQueue {
 static_assert(sizeof(WarpQueue) >= 16 * 32 * sizeof(float), "warp queue too small for the frame words");
 
 // Copy the double-float tables (only the rotation entries up to ring M)
-// from the parameter block into shared memory.
+// from the parameter block into shared memory (trace kernel).  The image
+// kernels read them in the parameter block itself, through the constant
+// cache: the shared copy's 9.5 KB per CTA are worth more as L1 for the
+// per-thread stack (two CTAs then fit the 164 KB shared configuration, which
+// leaves ~92 KB of L1 per SM instead of ~60 KB).
 __device__ __forceinline__ void load_tables(const KParams& P, Tables& T) {
     const int nwords = tables_words(P.M);
     const uint32_t* src = reinterpret_cast<const uint32_t*>(&P.tables);
@@ -273,11 +277,10 @@ __device__ __forceinline__ int tile_pixel() {
 template <int kMode>
 __global__ void __launch_bounds__(1024) fwd_kernel(const __grid_constant__ KParams P, const FrameDesc F) {
     extern __shared__ __align__(16) unsigned char smem[];
-    Tables& T = *reinterpret_cast<Tables*>(smem);
-    WarpQueue* Qs = reinterpret_cast<WarpQueue*>(smem + sizeof(Tables));
+    const Tables& T = P.tables;
+    WarpQueue* Qs = reinterpret_cast<WarpQueue*>(smem);
     uint32_t* ss0 = reinterpret_cast<uint32_t*>(Qs + blockDim.x / 32);
     float* suw = reinterpret_cast<float*>(ss0 + 12 * blockDim.x);
-    load_tables(P, T);
     WarpQueue& q = Qs[threadIdx.x >> 5];
     // Block-uniform tiles of blockDim.x pixels.  The barrier at the top of a
     // tile keeps the block's warps together in the (long, mostly
@@ -298,12 +301,11 @@ template <int kMode>
 __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KParams P,
                                                      const __grid_constant__ BatchDesc B) {
     extern __shared__ __align__(16) unsigned char smem[];
-    Tables& T = *reinterpret_cast<Tables*>(smem);
-    WarpQueue* Qs = reinterpret_cast<WarpQueue*>(smem + sizeof(Tables));
+    const Tables& T = P.tables;
+    WarpQueue* Qs = reinterpret_cast<WarpQueue*>(smem);
     uint32_t* ss0 = reinterpret_cast<uint32_t*>(Qs + blockDim.x / 32);
     float* suw = reinterpret_cast<float*>(ss0 + 12 * blockDim.x);
     __shared__ int tile_s;
-    load_tables(P, T);
     WarpQueue& q = Qs[threadIdx.x >> 5];
     for (int it = 0;; ++it) {
         __syncthreads();
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(1024) batch_kernel(const __grid_constant__ KPa
 }
 
 size_t fwd_smem_bytes(int threads) {
-    return sizeof(Tables) + (size_t)(threads / 32) * sizeof(WarpQueue) + (size_t)threads * 24 * sizeof(uint32_t);
+    return (size_t)(threads / 32) * sizeof(WarpQueue) + (size_t)threads * 24 * sizeof(uint32_t);
 }
 
 // --------------------------------------------------------------------------
