@@ -209,7 +209,9 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
                 // e.g. a half-vector far from the NDF's peak): its 12
                 // evaluations add nothing
                 if (!__any_sync(0xffffffffu, law.Tg > 1u)) continue;
-#pragma unroll
+                // (not unrolled: three copies of the queue-push code cost more
+                // in instruction-cache misses than the loop does)
+#pragma unroll 1
                 for (int j = 0; j < 3; ++j) {
                     const uint32_t s0 = s0s[(3 * i + j) * st], s1 = U.S1[3 * i + j];
                     const float uw = uws[(3 * i + j) * st] * shade_i;
