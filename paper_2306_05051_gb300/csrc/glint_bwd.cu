@@ -267,19 +267,14 @@ __device__ float pixel_grad(const KParams& P, const Tables& T, const FrameDesc& 
 // (L2 fit), grad_out is 2 (image - target) of the pixel's own image value,
 // which is written to out_img, and the loss sum (image - target)^2 is
 // reduced as component ng.
-__global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const __grid_constant__ KParams P, const FrameDesc F,
+__global__ void __launch_bounds__(kBwdThreads, 2) bwd_kernel(const __grid_constant__ KParams P, const FrameDesc F,
                                                           const float* grad_out, const float* target,
                                                           float* out_img, float* out_relaxed,
                                                           double* partial, int ng) {
-    __shared__ Tables T;
+    // the double-float tables are read in the parameter block (constant
+    // cache): no per-CTA copy, and the L1 keeps the shared memory it would take
+    const Tables& T = P.tables;
     __shared__ double red[kBwdThreads / 32][kMaxGrad + 1];
-    const int nwords = tables_words(P.M);
-    {
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(&P.tables);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(&T);
-        for (int k = threadIdx.x; k < nwords; k += blockDim.x) dst[k] = src[k];
-    }
-    __syncthreads();
     const int nc = target ? ng + 1 : ng;          // components reduced
     double mine[kMaxGrad + 1];
     for (int k = 0; k < nc; ++k) mine[k] = 0.0;
