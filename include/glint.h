@@ -252,7 +252,7 @@ int glint_backward(const GlintFrame* frame, const GlintMaterial* material, const
  * target[px]): the loss of an L2 fit depends on each pixel's own value only,
  * so grad_out of glint_backward is known inside the pixel.
  *   grad[k] = sum_px 2 (out[px] - target[px]) d relaxed(px) / d theta_k
- *   *loss   = sum_px (out[px] - target[px])^2      (FP64 sums, deterministic)
+ *   *loss   = sum_px (out[px] - target[px])^2      (double-float / FP64 sums, deterministic)
  * The paper fits nothing: this entry point serves the differentiable use of
  * the model (material and light fitting against a target image).
  *   target: device [height][width] float.   out: device [height][width] float.

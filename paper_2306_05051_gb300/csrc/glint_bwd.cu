@@ -11,9 +11,11 @@
 // differentiated in difference form, e.g. for the simplex weights
 //   sum_j du_j X_j = (qx/2)(X1 - X0) + (qy/2)(X2 - X1)   (d q / d ln rho = q/2),
 // which avoids cancelling the large +-q/2 terms.  Per-pixel terms are formed
-// in FP32; each thread's sums over its pixels are FP64, reduced per CTA in a
-// fixed order into the workspace, and a second kernel sums the CTA partials
-// in a fixed order: deterministic.
+// in FP32; each thread's sums over its pixels and the warp's shuffle tree are
+// double-float (exact products, Dekker sums: ~2^-44 of the summed magnitudes,
+// without the FP64 pipe, which is slow on this GPU), the warps' sums go to
+// FP64 and are reduced per CTA in a fixed order into the workspace, and a
+// second kernel sums the CTA partials in a fixed order: deterministic.
 #include "glint_kernels.cuh"
 
 namespace glint {
@@ -276,32 +278,35 @@ __global__ void __launch_bounds__(kBwdThreads, 2) bwd_kernel(const __grid_consta
     const Tables& T = P.tables;
     __shared__ double red[kBwdThreads / 32][kMaxGrad + 1];
     const int nc = target ? ng + 1 : ng;          // components reduced
-    double mine[kMaxGrad + 1];
-    for (int k = 0; k < nc; ++k) mine[k] = 0.0;
+    df mine[kMaxGrad + 1];
+    for (int k = 0; k < nc; ++k) mine[k] = mkdf(0.0f);
     const int stride = gridDim.x * blockDim.x;
     for (int px = blockIdx.x * blockDim.x + threadIdx.x; px < F.npx; px += stride) {
         float g[kMaxGrad], disc;
         const float o = pixel_grad(P, T, F, px, g, ng, &disc);
         if (out_relaxed) out_relaxed[px] = o;
-        double go;
+        float go;
         if (target) {
             const float r = disc - target[px];
             out_img[px] = disc;
-            go = 2.0 * (double)r;
-            mine[ng] += (double)r * (double)r;
+            go = 2.0f * r;
+            mine[ng] = mine[ng] + two_prod(r, r);
         } else {
-            go = (double)grad_out[px];
+            go = grad_out[px];
         }
-        if (go != 0.0)
-            for (int k = 0; k < ng; ++k) mine[k] += go * (double)g[k];
+        if (go != 0.0f)
+            for (int k = 0; k < ng; ++k) mine[k] = mine[k] + two_prod(go, g[k]);
     }
     // fixed-order reduction over the CTA: a shuffle tree per warp, then the
     // warps' sums in warp order
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int k = 0; k < nc; ++k) {
-        double v = mine[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[w][k] = v;
+        df v = mine[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const df u = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+            v = v + u;
+        }
+        if (lane == 0) red[w][k] = (double)v.hi + (double)v.lo;
     }
     __syncthreads();
     if ((int)threadIdx.x < nc) {
