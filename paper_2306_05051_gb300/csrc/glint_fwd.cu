@@ -82,11 +82,13 @@ __device__ __forceinline__ void load_tables(const KParams& P, Tables& T) {
 }
 
 // Evaluate the n <= 32 queue entries starting at `head`: lane k takes entry
-// head + k.  Each owner lane then adds its entries' values in queue order.
+// head + k.  Each owner lane then adds its entries' values in queue order to
+// its running sum, which goes in and comes back by value (a reference would
+// send it through the stack at every call).
 // kFinal: the queue holds the second hash word itself (table mode), else
 // its pre-image.
 template <bool kFinal>
-__device__ __noinline__ void flush_queue(WarpQueue& q, int head, int n, float& acc) {
+__device__ __noinline__ float flush_queue(WarpQueue& q, int head, int n, float acc) {
     const int lane = threadIdx.x & 31;
     const int e = (head + lane) & (kQ - 1);
     float val = 0.0f;
@@ -110,6 +112,7 @@ __device__ __noinline__ void flush_queue(WarpQueue& q, int head, int n, float& a
         mine &= mine - 1;
     }
     __syncwarp();
+    return acc;
 }
 
 struct LightEval {          // what the evaluation loop needs of one light
@@ -247,7 +250,7 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
                             count += __popc(m);
                             if (count >= 32) {
                                 __syncwarp();
-                                flush_queue<kTable>(q, head, 32, acc);
+                                acc = flush_queue<kTable>(q, head, 32, acc);
                                 head = (head + 32) & (kQ - 1);
                                 count -= 32;
                             }
@@ -259,7 +262,7 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
     }
     if (count > 0) {
         __syncwarp();
-        flush_queue<kTable>(q, head, count, acc);
+        acc = flush_queue<kTable>(q, head, count, acc);
     }
     if (S.status != 0 || !in_range) return 0.0f;
     return acc / S.A.hi;
