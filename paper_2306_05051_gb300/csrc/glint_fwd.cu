@@ -152,7 +152,7 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
     const float n_max = fmaxf(fmaxf(S.ntr[0], S.ntr[1]), fmaxf(S.ntr[2], S.ntr[3]));
     for (int l = 0; l < F.nL; ++l) {
         ls[l].on = false;
-        if (S.status == 0) setup_light<false>(P, T, F, S, R, px, l, ls[l]);
+        if (S.status == 0) setup_light<false, SharedFrame, false>(P, T, F, S, R, px, l, ls[l]);
         if (ls[l].on && ls[l].p < 1.0f && !kClassical && -expm1f(n_max * ls[l].lq) <= 1.4901161193847656e-8f)
             ls[l].on = false;
         any_on |= ls[l].on;
@@ -185,8 +185,11 @@ __device__ float shade_warp(const KParams& P, const Tables& T, const FrameDesc& 
             L.on = act && ls[l].on;
             L.p = ls[l].p; L.p_lo = ls[l].p_lo; L.lq = ls[l].lq; L.shade = ls[l].shade;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) { L.v[k] = ls[l].v[k]; L.A0[k] = ls[l].A0[k]; L.A1[k] = ls[l].A1[k]; }
+            for (int k = 0; k < 4; ++k) L.v[k] = ls[l].v[k];
             if (!__any_sync(0xffffffffu, L.on)) continue;
+            // the angular words are formed here from the texel rather than
+            // stored per light (less stack)
+            angular_words(P, ls[l].ix0, ls[l].iy0, L.A0, L.A1);
 #pragma unroll 1
             for (int ii = 0; ii < (kIso ? 2 : 4); ++ii) {
                 const int i = kIso ? 3 * ii : ii;

@@ -553,13 +553,27 @@ struct LightState {
     float p_lo;                   // low word of p (double-float where the counts can be large)
     float lq;                     // log(1 - p) (count laws)
     float v[4];                   // angular bilinear weights
-    uint32_t A0[4], A1[4];        // angular hash words
+    uint32_t A0[4], A1[4];        // angular hash words (kWords)
+    int32_t ix0, iy0;             // angular texel of corner 0
     int32_t ax[4], ay[4];         // angular texels (traces)
 };
 
+// The four angular hash words of the texels (ix0 + (k & 1), iy0 + (k >> 1)).
+__device__ __forceinline__ void angular_words(const KParams& P, int ix0, int iy0, uint32_t A0[4], uint32_t A1[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t hx = (uint32_t)(ix0 + (k & 1)), hy = (uint32_t)(iy0 + (k >> 1)), hz = ~P.seed;
+        pcg3d(hx, hy, hz);
+        A0[k] = hx; A1[k] = hy;
+    }
+}
+
 // kTrace: also record the angular texels (ax, ay) for the trace and adjoint
-// kernels; the image kernels skip those stores.
-template <bool kTrace, class FS>
+// kernels; the image kernels skip those stores.  kWords: also store the four
+// angular hash words; the image kernels form them in the evaluation loop
+// from the stored texel (ix0, iy0) instead, which keeps 6 words per light off
+// the per-thread stack for the same work when a pixel has one sub-footprint.
+template <bool kTrace, class FS, bool kWords = true>
 static __device__ __forceinline__ void setup_light(const KParams& P, const Tables& T, const FrameDesc& F,
                                                    const PixelSetup& S, const FS& R, int px, int l, LightState& L) {
     L.on = false;
@@ -628,13 +642,12 @@ static __device__ __forceinline__ void setup_light(const KParams& P, const Table
     const int iy = dffloor_w(div_by(h[1], P.gamma, ig), &fy, &gy);
     L.v[0] = gx * gy; L.v[1] = fx * gy;
     L.v[2] = gx * fy; L.v[3] = fx * fy;
+    L.ix0 = ix; L.iy0 = iy;
+    if (kTrace) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (kTrace) { L.ax[k] = ix + (k & 1); L.ay[k] = iy + (k >> 1); }
-        uint32_t hx = (uint32_t)(ix + (k & 1)), hy = (uint32_t)(iy + (k >> 1)), hz = ~P.seed;
-        pcg3d(hx, hy, hz);
-        L.A0[k] = hx; L.A1[k] = hy;
+        for (int k = 0; k < 4; ++k) { L.ax[k] = ix + (k & 1); L.ay[k] = iy + (k >> 1); }
     }
+    if (kWords) angular_words(P, ix, iy, L.A0, L.A1);
     // Eq. 2 with D_P = D(n)/R C/A: out_l = F G D(n) E / (4 R cos_v) * C / A
     const float vh = wv[0].hi * ht + wv[1].hi * hb + cos_v * hn;
     const float om = 1.0f - vh;
