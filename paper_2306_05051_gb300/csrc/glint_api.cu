@@ -163,6 +163,7 @@ FrameDesc make_frame_desc(const GlintFrame* f, float* out) {
     F.out = out;
     F.W = f->width; F.H = f->height; F.npx = f->width * f->height; F.nL = f->n_lights;
     F.lstride = F.npx;
+    F.tile_w = 0;
     return F;
 }
 

@@ -53,7 +53,7 @@ void fill_batch(GlintContext* c, const GlintFrame* frames, int n, float* const* 
     for (int f = 0; f < n; ++f) {
         B.frames[f] = make_frame_desc(&frames[f], outs[f]);
         B.tile_base[f] = t;
-        t += (B.frames[f].npx + threads - 1) / threads;
+        t += frame_tiles(B.frames[f], threads);
     }
     B.tile_base[n] = t;
 }
@@ -206,7 +206,7 @@ int glint_eval_batch(GlintContext* c, const GlintFrame* frames, int32_t n_frames
         nl_max = frames[f].n_lights > nl_max ? frames[f].n_lights : nl_max;
         tiles_min += ((long long)frames[f].width * frames[f].height + 1023) / 1024;
     }
-    if (tiles_min * 8 > 0x7fffffffLL) return GLINT_ERR_ARG;
+    if (tiles_min * 16 > 0x7fffffffLL) return GLINT_ERR_ARG;     // 128-pixel tiles, with 2-D padding
     int rc = make_material_params(material, lights, nl_max, &c->P);
     if (rc) return rc;
     for (int f = 0; f < n_frames; ++f) {

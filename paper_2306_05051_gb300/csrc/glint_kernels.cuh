@@ -17,6 +17,10 @@ constexpr int kMaxBatch = 128;
 
 // Frames of one persistent batched launch (passed by value as a kernel
 // parameter, so a graph node can be re-pointed without re-capture).
+// Tiles of a frame for CTAs of `threads` threads: chooses F.tile_w (row tiles
+// or 2-D blocks) and returns the number of tiles.
+int frame_tiles(FrameDesc& F, int threads);
+
 struct BatchDesc {
     int32_t n;
     int32_t persistent;                 // 1: CTAs take tiles from the counter; 0: CTA b shades tile b

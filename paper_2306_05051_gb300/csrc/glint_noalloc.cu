@@ -82,7 +82,7 @@ extern "C" int glint_eval_batch_noalloc(const GlintFrame* frames, int32_t n_fram
         for (int k = 0; k < n; ++k) {
             B.frames[k] = make_frame_desc(&frames[f0 + k], outs[f0 + k]);
             B.tile_base[k] = (int)t;
-            t += (B.frames[k].npx + kNoallocLaunch.threads_per_cta - 1) / kNoallocLaunch.threads_per_cta;
+            t += frame_tiles(B.frames[k], kNoallocLaunch.threads_per_cta);
             if (t > 0x7fffffffLL) return GLINT_ERR_ARG;
         }
         B.tile_base[n] = (int)t;

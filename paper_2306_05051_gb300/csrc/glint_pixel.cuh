@@ -67,6 +67,8 @@ struct FrameDesc {
     float* out;
     int32_t W, H, npx, nL;
     int32_t lstride;             // pixels between the planes of consecutive lights (npx, or more for a band)
+    int32_t tile_w;              // 0: a CTA's tile is blockDim.x consecutive pixels; else a block of
+                                 // tile_w x (blockDim.x / tile_w) pixels (frame_tiles chooses)
 };
 
 // Material, lights and tables, shared by every frame of a launch.
