@@ -255,6 +255,21 @@ def test_every_launch_shape_gives_the_same_bits():
         assert e.value.code == -1, bad
 
 
+def test_launch_shapes_across_row_and_block_tiles():
+    """A frame large enough that some launch shapes tile it in 16-pixel-wide
+    blocks (at least 2048 row tiles) and others in runs of a row: every
+    shape, one CTA per tile or persistent, gives the same bits, and every
+    pixel is written."""
+    sc = scenes.sphere_plane(1600, 900, seed=6)               # 1.44 M px: 2-D at 128-512 threads, rows at 1024
+    scd = sc.to(DEV)
+    ref = glint.render_scene(scd)
+    for shape in [(128, 0), (256, 0), (1024, 0), (512, 2), (256, 4), (128, 8), (1024, 1)]:
+        img = torch.full_like(ref, float("nan"))
+        glint.render_scene(scd, out=img, launch=shape)
+        torch.cuda.synchronize()
+        assert torch.equal(img, ref), shape
+
+
 def _iso(sc):
     import dataclasses
     return dataclasses.replace(sc, material=dataclasses.replace(sc.material, n_rings=0))
