@@ -129,8 +129,7 @@ cudaError_t capture_graph(GlintContext* c) {
 cudaError_t update_graph(GlintContext* c) {
     const FwdLaunch cfg = batch_launch(c->B, c->launch);
     void* args[2] = {&c->P, &c->B};
-    cudaKernelNodeParams kp;
-    std::memset(&kp, 0, sizeof(kp));
+    cudaKernelNodeParams kp{};
     kp.func = const_cast<void*>(batch_kernel_fn(kernel_variant(c->P)));
     kp.gridDim = dim3(cfg.blocks);
     kp.blockDim = dim3(cfg.threads);
